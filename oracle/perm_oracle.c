@@ -1,0 +1,529 @@
+/*
+ * perm_oracle.c -- plain, slow, single-threaded CPU reference for interacting
+ * flatPERM on the square (d = 2) and cubic (d = 3) lattices.
+ *
+ * TEST INFRASTRUCTURE ONLY: tests, the smoke check and the CPU-baseline leg of
+ * the benchmark load it; the product path never does.  It shares no code with
+ * the CUDA path.  Build with -ffp-contract=off so that no multiply-add is fused
+ * (every floating-point operation below is one IEEE round-to-nearest step).
+ *
+ * Paper: Campbell and Janse van Rensburg, "Parallel PERM".
+ *
+ * What each part follows, and how it is pinned (tests under tests/):
+ *  - orc_philox4x32_10: Philox4x32 with 10 rounds, from Salmon et al.,
+ *    "Parallel random numbers: as easy as 1, 2, 3" (SC'11).  Pinned by the
+ *    published known-answer vectors (tests/golden/philox4x32_10_kat.txt).
+ *  - orc_enumerate: c_n by brute-force depth-first enumeration of all
+ *    self-avoiding walks (the quantity of Sec. 1, eq. 3).  Pinned by closed
+ *    forms for n <= 4, by an independent pure-Python brute force for small n,
+ *    and by lattice symmetry.
+ *  - node growth (orc_step / the run loop): Rosenbluth growth (Sec. 1, eqs.
+ *    1-2), flatPERM ratio, enrichment and pruning (Sec. 2, eq. 6 and the
+ *    paragraphs after it).  Pinned by exact c_0..c_3 in every run, by the
+ *    counting theorem (Sec. 1, eq. 3: estimates within 4 sigma of the exact
+ *    c_n from orc_enumerate), by weight conservation under enrichment, by the
+ *    survival probability of pruning, and by the uniformity of the chosen
+ *    directions.
+ *  - variance estimate: per-tour sums (the paper gives no error bars); pinned
+ *    by the z-score calibration of the estimates against exact c_n over many
+ *    seeds.
+ *
+ * Readings of the paper taken here (each also listed in the design doc):
+ *  - The weight entering r is W(omega_k) before multiplication by
+ *    a_+(omega_k); the children carry W'.a_+ (Sec. 2 with eq. 2).
+ *  - M counts every tour started so far, the current one included; the own
+ *    weight is included in the running average (Sec. 2; Sec. 3, Alg. 2).
+ *  - r is 1 at the empty walk, so every tour has exactly one node of length 0
+ *    and one of length 1.
+ *  - r is evaluated in single precision by the recipe in orc_ratio (the
+ *    decision precision of the GPU kernel); weights stay in double precision.
+ *  - Enriched copies take distinct steps, c is capped at a_+, each child has
+ *    weight (W/c).a_+.  Survival after pruning has probability q = K/2^32 with
+ *    K = ceil(r 2^32), and the survivor carries W/q (so the estimator stays
+ *    exactly unbiased for the quantised r).
+ *  - Random numbers: one Philox4x32-10 block per node, counter = (DFS ordinal
+ *    of the node within its tour, 64 bit; tour index; sequence index), key =
+ *    (low seed word XOR run id, high seed word).  Word 0 decides c (or
+ *    survival), word 1 picks the c distinct directions by a partial
+ *    Fisher-Yates shuffle with batched multiply-high draws.
+ *  - Directions are ordered +x, -x, +y, -y, +z, -z; the first chosen child is
+ *    grown first and the others wait on the stack in order.
+ *  - Weights are stored divided by 2^E(n), E(n) = floor(11n/8) (d = 2) or
+ *    floor(9n/4) (d = 3), so that they stay inside the double range at long
+ *    lengths; r is scale free and log c_n adds E(n) log 2 back.
+ *  - Alg. 2 executed by one thread runs the tours of all sequences one after
+ *    another; tour g (counted from 0) belongs to sequence g mod N, tour g div N.
+ */
+#include "perm_oracle.h"
+
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+/* ------------------------------------------------------------------------- */
+/* Philox4x32-10 (Salmon et al., SC'11, Sec. 3 and its Table 2 constants).    */
+/* One round: two 32x32->64 multiplies of words 0 and 2; the high halves are  */
+/* XORed with the other words and the round key, words are permuted.  The key */
+/* is bumped by the Weyl constants between rounds.                            */
+/* ------------------------------------------------------------------------- */
+#define PHILOX_M4x32_0 0xD2511F53u
+#define PHILOX_M4x32_1 0xCD9E8D57u
+#define PHILOX_W32_0 0x9E3779B9u
+#define PHILOX_W32_1 0xBB67AE85u
+
+void orc_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]) {
+    uint32_t x0 = ctr[0], x1 = ctr[1], x2 = ctr[2], x3 = ctr[3];
+    uint32_t k0 = key[0], k1 = key[1];
+    for (int round = 0; round < 10; ++round) {
+        if (round > 0) {
+            k0 += PHILOX_W32_0;
+            k1 += PHILOX_W32_1;
+        }
+        uint64_t p0 = (uint64_t)PHILOX_M4x32_0 * (uint64_t)x0;
+        uint64_t p1 = (uint64_t)PHILOX_M4x32_1 * (uint64_t)x2;
+        uint32_t hi0 = (uint32_t)(p0 >> 32), lo0 = (uint32_t)p0;
+        uint32_t hi1 = (uint32_t)(p1 >> 32), lo1 = (uint32_t)p1;
+        uint32_t y0 = hi1 ^ x1 ^ k0;
+        uint32_t y1 = lo1;
+        uint32_t y2 = hi0 ^ x3 ^ k1;
+        uint32_t y3 = lo0;
+        x0 = y0; x1 = y1; x2 = y2; x3 = y3;
+    }
+    out[0] = x0; out[1] = x1; out[2] = x2; out[3] = x3;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Exact enumeration (Sec. 1: c_n, the number of n-step self-avoiding walks). */
+/* ------------------------------------------------------------------------- */
+static void enum_rec(int d, int n, int depth, int *pos, unsigned char *occ,
+                     const long *stride, int64_t *c) {
+    c[depth] += 1;
+    if (depth == n) return;
+    for (int axis = 0; axis < d; ++axis) {
+        for (int sgn = 1; sgn >= -1; sgn -= 2) {
+            pos[axis] += sgn;
+            long idx = 0;
+            for (int i = 0; i < d; ++i) idx += (long)(pos[i] + n + 1) * stride[i];
+            if (!occ[idx]) {
+                occ[idx] = 1;
+                enum_rec(d, n, depth + 1, pos, occ, stride, c);
+                occ[idx] = 0;
+            }
+            pos[axis] -= sgn;
+        }
+    }
+}
+
+int orc_enumerate(int d, int n, int64_t *c_out) {
+    if ((d != 2 && d != 3) || n < 0 || n > 24 || !c_out) return ORC_EINVAL;
+    long side = 2L * n + 3;
+    long total = 1, stride[3] = {1, 1, 1};
+    for (int i = 0; i < d; ++i) { stride[i] = total; total *= side; }
+    unsigned char *occ = (unsigned char *)calloc((size_t)total, 1);
+    if (!occ) return ORC_ENOMEM;
+    int pos[3] = {0, 0, 0};
+    for (int k = 0; k <= n; ++k) c_out[k] = 0;
+    long origin = 0;
+    for (int i = 0; i < d; ++i) origin += (long)(n + 1) * stride[i];
+    occ[origin] = 1;
+    enum_rec(d, n, 0, pos, occ, stride, c_out);
+    free(occ);
+    return ORC_OK;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Weight scale and the ratio r.                                              */
+/* ------------------------------------------------------------------------- */
+int orc_scale_exp(int d, int n) { return d == 2 ? (11 * n) / 8 : (9 * n) / 4; }
+
+/* a/b for finite a >= 0, b > 0 in single precision: both mantissas are cut to
+ * 24 bits, divided in FP32 (round to nearest), and the exponent difference
+ * (clamped to [-100, 100]) is applied exactly. */
+static float ratio_f32(double a, double b) {
+    uint64_t ab, bb;
+    memcpy(&ab, &a, 8);
+    memcpy(&bb, &b, 8);
+    int ea_f = (int)((ab >> 52) & 0x7FF), eb_f = (int)((bb >> 52) & 0x7FF);
+    if (ea_f == 0) return 0.0f;                        /* a zero (or subnormal) */
+    if (eb_f == 0) return 1.2676506e30f;               /* 2^100: b zero or subnormal */
+    uint32_t fa_bits = (127u << 23) | (uint32_t)((ab & 0xFFFFFFFFFFFFFull) >> 29);
+    uint32_t fb_bits = (127u << 23) | (uint32_t)((bb & 0xFFFFFFFFFFFFFull) >> 29);
+    float fa, fb;
+    memcpy(&fa, &fa_bits, 4);
+    memcpy(&fb, &fb_bits, 4);
+    float q = fa / fb;                                 /* in (0.5, 2) */
+    int e = ea_f - eb_f;
+    if (e > 100) e = 100;
+    if (e < -100) e = -100;
+    uint32_t p2_bits = (uint32_t)(e + 127) << 23;
+    float p2;
+    memcpy(&p2, &p2_bits, 4);
+    return q * p2;                                     /* exact power-of-two scaling */
+}
+
+/* r = W / [W_n]^sample with the own weight included (Sec. 2, eq. 6):
+ * [W_n] = (sum of earlier weights + W) / M = T + W/M, so r = 1 / (T/W + 1/M). */
+float orc_ratio(int n, double W, double T, int64_t M) {
+    if (n == 0) return 1.0f;
+    float Mf = (float)M;
+    float invM = 1.0f / Mf;
+    float rho = ratio_f32(T, W);
+    float x = rho + invM;
+    return 1.0f / x;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Occupancy of the current walk: a dense byte box when it is small enough,   */
+/* else a linear scan of the walk's sites.                                    */
+/* ------------------------------------------------------------------------- */
+typedef struct {
+    int d, n_max;
+    long side, stride[3];
+    unsigned char *box;     /* NULL => linear scan */
+    const int32_t *coords;  /* walk sites, (n+1)*d */
+    int n;                  /* current endpoint index (for the scan) */
+} occset;
+
+static int occ_init(occset *o, int d, int n_max) {
+    o->d = d; o->n_max = n_max; o->box = NULL; o->coords = NULL; o->n = -1;
+    o->side = 2L * n_max + 3;
+    long total = 1;
+    for (int i = 0; i < d; ++i) { o->stride[i] = total; total *= o->side; }
+    if (total <= (1L << 26)) {
+        o->box = (unsigned char *)calloc((size_t)total, 1);
+        if (!o->box) return ORC_ENOMEM;
+    }
+    return ORC_OK;
+}
+
+static long occ_index(const occset *o, const int32_t *p) {
+    long idx = 0;
+    for (int i = 0; i < o->d; ++i) idx += (long)(p[i] + o->n_max + 1) * o->stride[i];
+    return idx;
+}
+
+static int occ_has(const occset *o, const int32_t *p) {
+    if (o->box) return o->box[occ_index(o, p)];
+    for (int k = 0; k <= o->n; ++k) {
+        int same = 1;
+        for (int i = 0; i < o->d; ++i) same &= (o->coords[k * o->d + i] == p[i]);
+        if (same) return 1;
+    }
+    return 0;
+}
+
+static void occ_set(occset *o, const int32_t *p, unsigned char v) {
+    if (o->box) o->box[occ_index(o, p)] = v;
+}
+
+/* unit step j: axis j/2, sign + for even j */
+static void add_step(int d, const int32_t *from, int j, int32_t *to) {
+    for (int i = 0; i < d; ++i) to[i] = from[i];
+    to[j >> 1] += (j & 1) ? -1 : 1;
+}
+
+/* ------------------------------------------------------------------------- */
+/* One node: a_+, r, the enrichment/pruning decision, the distinct steps and  */
+/* the children's weight (Sec. 1 eqs. 1-2; Sec. 2).                           */
+/* ------------------------------------------------------------------------- */
+typedef struct {
+    int a_plus, free_mask, c, dirs[6];
+    float r;
+    double child_w;
+    uint64_t survive_K;
+} node_out;
+
+static int grow_node(int d, int n_max, int n, const int32_t *end, const occset *occ,
+                     double W, double T, int64_t M, uint64_t ordinal, uint32_t seq,
+                     uint32_t tour, uint64_t seed, uint32_t run, node_out *o) {
+    o->a_plus = 0; o->free_mask = 0; o->c = 0; o->r = 0.0f; o->child_w = 0.0;
+    o->survive_K = 0;
+    if (n == n_max) return ORC_LEAF_NMAX;                     /* walk complete */
+
+    /* a_+: the free neighbours of the end-point (Sec. 1) */
+    int free_list[6], a = 0;
+    for (int j = 0; j < 2 * d; ++j) {
+        int32_t nb[3];
+        add_step(d, end, j, nb);
+        if (!occ_has(occ, nb)) {
+            free_list[a++] = j;
+            o->free_mask |= 1 << j;
+        }
+    }
+    o->a_plus = a;
+    if (a == 0) return ORC_LEAF_TRAPPED;                       /* trapped: weight 0 beyond */
+
+    /* r (Sec. 2, eq. 6) and the node's random block */
+    float r = orc_ratio(n, W, T, M);
+    o->r = r;
+    uint32_t ctr[4] = {(uint32_t)ordinal, (uint32_t)(ordinal >> 32), tour, seq};
+    uint32_t key[2] = {(uint32_t)seed ^ run, (uint32_t)(seed >> 32)};
+    uint32_t w[4];
+    orc_philox4x32_10(ctr, key, w);
+
+    int c;
+    double Wp;
+    if (r >= 1.0f) {
+        /* enrichment: p = ceil(r) - r; c = floor(r) with probability p, else ceil(r) */
+        float fl = floorf(r), ce = ceilf(r);
+        float p = ce - r;
+        uint64_t Kp = (uint64_t)ceilf(p * 4294967296.0f);   /* u0 < p  <=>  w0 < Kp */
+        float c_raw = ((uint64_t)w[0] < Kp) ? fl : ce;
+        c = (c_raw >= (float)a) ? a : (int)c_raw;             /* distinct steps: at most a_+ */
+        Wp = W / (double)c;                                   /* each copy carries W/c */
+    } else {
+        /* pruning: survive with probability q = K/2^32 (K = ceil(r 2^32)), weight W/q */
+        uint64_t K = (uint64_t)ceilf(r * 4294967296.0f);
+        o->survive_K = K;
+        if (!((uint64_t)w[0] < K)) return ORC_LEAF_PRUNED;
+        c = 1;
+        Wp = (W * 4294967296.0) / (double)K;
+    }
+
+    /* c distinct directions: partial Fisher-Yates over the free list, draws from word 1 */
+    uint32_t x = w[1];
+    for (int i = 0; i < c; ++i) {
+        uint32_t m = (uint32_t)(a - i);
+        uint64_t prod = (uint64_t)x * m;
+        int j = i + (int)(prod >> 32);
+        x = (uint32_t)prod;
+        int tmp = free_list[i]; free_list[i] = free_list[j]; free_list[j] = tmp;
+    }
+    for (int i = 0; i < c; ++i) o->dirs[i] = free_list[i];
+    o->c = c;
+    /* each child: W' a_+ (eq. 2), stored at the scale of length n+1 */
+    int dE = orc_scale_exp(d, n + 1) - orc_scale_exp(d, n);
+    o->child_w = ldexp(Wp * (double)a, -dE);
+    return ORC_CHILDREN;
+}
+
+int orc_step(int d, int n_max, int n, const int32_t *coords, double W, double T,
+             int64_t M, uint64_t ordinal, uint32_t seq, uint32_t tour,
+             uint64_t seed, uint32_t run,
+             int *a_plus, int *free_mask, float *r, int *c, int *dirs,
+             double *child_w, uint64_t *survive_K) {
+    if ((d != 2 && d != 3) || n < 0 || n > n_max || n_max < 1 || !coords || M < 1)
+        return ORC_EINVAL;
+    /* the snapshot must be a self-avoiding walk from the origin */
+    for (int i = 0; i < d; ++i) if (coords[i] != 0) return ORC_EINVAL;
+    for (int k = 1; k <= n; ++k) {
+        int dist = 0;
+        for (int i = 0; i < d; ++i) dist += abs(coords[k * d + i] - coords[(k - 1) * d + i]);
+        if (dist != 1) return ORC_EINVAL;
+        for (int l = 0; l < k; ++l) {
+            int same = 1;
+            for (int i = 0; i < d; ++i) same &= (coords[k * d + i] == coords[l * d + i]);
+            if (same) return ORC_EINVAL;
+        }
+    }
+    occset occ;
+    occ.d = d; occ.n_max = n_max; occ.box = NULL; occ.coords = coords; occ.n = n;
+    node_out o;
+    int rc = grow_node(d, n_max, n, coords + (long)n * d, &occ, W, T, M, ordinal, seq,
+                       tour, seed, run, &o);
+    if (a_plus) *a_plus = o.a_plus;
+    if (free_mask) *free_mask = o.free_mask;
+    if (r) *r = o.r;
+    if (c) *c = o.c;
+    if (dirs) for (int i = 0; i < o.c; ++i) dirs[i] = o.dirs[i];
+    if (child_w) *child_w = o.child_w;
+    if (survive_K) *survive_K = o.survive_K;
+    return rc;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Simulation state: the shared table W (Alg. 2) or one table per sequence    */
+/* (Alg. 1), the running walk, and the stack of waiting copies.               */
+/* ------------------------------------------------------------------------- */
+typedef struct { int depth, dir; double w; } stack_rec;
+
+struct orc_state {
+    int d, n_max, n_seq, alg;
+    uint64_t seed;
+    uint32_t run;
+    int ntab;              /* 1 (Alg. 2) or n_seq (Alg. 1) */
+    double *Wn, *Qn;       /* ntab * (n_max+1) */
+    int64_t *Sn;           /* ntab * (n_max+1) */
+    int64_t *M;            /* ntab: tours started */
+    int64_t *tours_done;   /* n_seq (Alg. 1); [0] counts tickets for Alg. 2 */
+    double *X;             /* n_max+1: this tour's weight per length */
+    int32_t *coords;       /* (n_max+1)*d */
+    stack_rec *stack;
+    long stack_cap;
+    occset occ;
+    int64_t steps, max_stack;
+};
+
+void orc_destroy(orc_state *h) {
+    if (!h) return;
+    free(h->Wn); free(h->Qn); free(h->Sn); free(h->M); free(h->tours_done);
+    free(h->X); free(h->coords); free(h->stack); free(h->occ.box);
+    free(h);
+}
+
+int orc_create(orc_state **out, int d, int n_max, int n_seq, uint64_t seed,
+               uint32_t run, int alg) {
+    if (!out) return ORC_EINVAL;
+    *out = NULL;
+    if ((d != 2 && d != 3) || n_max < 1 || n_max > 100000 || n_seq < 1 ||
+        (alg != ORC_ALG1 && alg != ORC_ALG2))
+        return ORC_EINVAL;
+    orc_state *h = (orc_state *)calloc(1, sizeof(orc_state));
+    if (!h) return ORC_ENOMEM;
+    h->d = d; h->n_max = n_max; h->n_seq = n_seq; h->alg = alg; h->seed = seed; h->run = run;
+    h->ntab = (alg == ORC_ALG1) ? n_seq : 1;
+    size_t L = (size_t)n_max + 1;
+    h->Wn = (double *)calloc(L * h->ntab, sizeof(double));
+    h->Qn = (double *)calloc(L * h->ntab, sizeof(double));
+    h->Sn = (int64_t *)calloc(L * h->ntab, sizeof(int64_t));
+    h->M = (int64_t *)calloc((size_t)h->ntab, sizeof(int64_t));
+    h->tours_done = (int64_t *)calloc((size_t)n_seq, sizeof(int64_t));
+    h->X = (double *)calloc(L, sizeof(double));
+    h->coords = (int32_t *)calloc(L * d, sizeof(int32_t));
+    h->stack_cap = (long)n_max * (2 * d - 2) + 2 * d;
+    h->stack = (stack_rec *)calloc((size_t)h->stack_cap, sizeof(stack_rec));
+    if (!h->Wn || !h->Qn || !h->Sn || !h->M || !h->tours_done || !h->X || !h->coords ||
+        !h->stack || occ_init(&h->occ, d, n_max) != ORC_OK) {
+        orc_destroy(h);
+        return ORC_ENOMEM;
+    }
+    h->occ.coords = h->coords;
+    *out = h;
+    return ORC_OK;
+}
+
+/* One tour: start at the empty walk and grow depth first until every copy has
+ * ended (Sec. 2).  M is the number of tours started on this table, this one
+ * included (Sec. 1, eq. 4; Sec. 3, Alg. 2). */
+static int run_tour(orc_state *h, int tab, uint32_t seq, uint32_t tour, int64_t M) {
+    const int d = h->d, n_max = h->n_max;
+    double *Wn = h->Wn + (size_t)tab * (n_max + 1);
+    double *Qn = h->Qn + (size_t)tab * (n_max + 1);
+    int64_t *Sn = h->Sn + (size_t)tab * (n_max + 1);
+    int32_t *co = h->coords;
+    long sp = 0;
+    int n = 0;
+    double W = 1.0;
+    uint64_t ordinal = 0;
+    for (int i = 0; i < d; ++i) co[i] = 0;
+    h->occ.n = 0;
+    occ_set(&h->occ, co, 1);
+    for (;;) {
+        /* running average before this node, then accumulate the node (eq. 4) */
+        double T = Wn[n] / (double)M;
+        Wn[n] += W;
+        Sn[n] += 1;
+        h->X[n] += W;
+        h->steps += 1;
+        node_out o;
+        int rc = grow_node(d, n_max, n, co + (long)n * d, &h->occ, W, T, M, ordinal,
+                           seq, tour, h->seed, h->run, &o);
+        ordinal += 1;
+        if (rc == ORC_CHILDREN) {
+            /* copies 1..c-1 wait on the stack (copy 1 on top); copy 0 grows now */
+            for (int i = o.c - 1; i >= 1; --i) {
+                if (sp >= h->stack_cap) return ORC_EOVERFLOW;
+                h->stack[sp].depth = n;
+                h->stack[sp].dir = o.dirs[i];
+                h->stack[sp].w = o.child_w;
+                ++sp;
+            }
+            if (sp > h->max_stack) h->max_stack = sp;
+            add_step(d, co + (long)n * d, o.dirs[0], co + (long)(n + 1) * d);
+            n += 1;
+            h->occ.n = n;
+            occ_set(&h->occ, co + (long)n * d, 1);
+            W = o.child_w;
+            continue;
+        }
+        /* leaf: resume the most recent waiting copy, or end the tour */
+        if (sp == 0) break;
+        --sp;
+        int dp = h->stack[sp].depth;
+        for (int k = n; k > dp; --k) occ_set(&h->occ, co + (long)k * d, 0);
+        add_step(d, co + (long)dp * d, h->stack[sp].dir, co + (long)(dp + 1) * d);
+        n = dp + 1;
+        h->occ.n = n;
+        occ_set(&h->occ, co + (long)n * d, 1);
+        W = h->stack[sp].w;
+    }
+    for (int k = n; k >= 0; --k) occ_set(&h->occ, co + (long)k * d, 0);
+    h->occ.n = -1;
+    /* per-tour sums for the variance estimate */
+    for (int k = 0; k <= n_max; ++k) {
+        Qn[k] += h->X[k] * h->X[k];
+        h->X[k] = 0.0;
+    }
+    return ORC_OK;
+}
+
+int orc_run(orc_state *h, int64_t tours_per_seq) {
+    if (!h || tours_per_seq < 0) return ORC_EINVAL;
+    if (h->alg == ORC_ALG2) {
+        /* Alg. 2 run by one thread: all sequences' tours in ticket order */
+        int64_t first = h->M[0], last = h->M[0] + tours_per_seq * (int64_t)h->n_seq;
+        for (int64_t g = first; g < last; ++g) {
+            uint32_t seq = (uint32_t)(g % h->n_seq), tour = (uint32_t)(g / h->n_seq);
+            h->M[0] = g + 1;
+            int rc = run_tour(h, 0, seq, tour, h->M[0]);
+            if (rc != ORC_OK) return rc;
+        }
+        h->tours_done[0] = h->M[0];
+    } else {
+        /* Alg. 1: every sequence against its own table */
+        for (int s = 0; s < h->n_seq; ++s) {
+            for (int64_t i = 0; i < tours_per_seq; ++i) {
+                int64_t t = h->tours_done[s];
+                h->M[s] = t + 1;
+                int rc = run_tour(h, s, (uint32_t)s, (uint32_t)t, h->M[s]);
+                if (rc != ORC_OK) return rc;
+                h->tours_done[s] = t + 1;
+            }
+        }
+    }
+    return ORC_OK;
+}
+
+int orc_tables(const orc_state *h, double *Wn, double *Sn, double *Qn,
+               int64_t *M_out, int64_t *steps, int64_t *max_stack) {
+    if (!h) return ORC_EINVAL;
+    size_t L = (size_t)(h->n_max + 1) * h->ntab;
+    for (size_t i = 0; i < L; ++i) {
+        if (Wn) Wn[i] = h->Wn[i];
+        if (Sn) Sn[i] = (double)h->Sn[i];
+        if (Qn) Qn[i] = h->Qn[i];
+    }
+    if (M_out) for (int t = 0; t < h->ntab; ++t) M_out[t] = h->M[t];
+    if (steps) *steps = h->steps;
+    if (max_stack) *max_stack = h->max_stack;
+    return ORC_OK;
+}
+
+/* log c_n from <W_n> = W_n / M (eq. 4; Alg. 1 averages the sequences' own
+ * estimates, eq. 7), S_n, and the relative variance of the estimate from the
+ * per-tour sums: var = (Q/M - c^2)/(M - 1). */
+int orc_estimates(const orc_state *h, double *log_cn, double *S_n, double *relvar_n) {
+    if (!h) return ORC_EINVAL;
+    const int L = h->n_max + 1;
+    for (int n = 0; n < L; ++n) {
+        double est = 0.0, var = 0.0, s = 0.0;
+        int ok = 1;
+        for (int t = 0; t < h->ntab; ++t) {
+            int64_t M = h->M[t];
+            double Wt = h->Wn[(size_t)t * L + n], Qt = h->Qn[(size_t)t * L + n];
+            s += (double)h->Sn[(size_t)t * L + n];
+            if (M < 2) { ok = 0; continue; }
+            double c = Wt / (double)M;
+            double v = (Qt / (double)M - c * c) / (double)(M - 1);
+            if (v < 0.0) v = 0.0;
+            est += c;
+            var += v;
+        }
+        est /= (double)h->ntab;
+        var /= (double)h->ntab * (double)h->ntab;
+        if (log_cn) log_cn[n] = (est > 0.0) ? log(est) + orc_scale_exp(h->d, n) * log(2.0) : -INFINITY;
+        if (S_n) S_n[n] = s;
+        if (relvar_n) relvar_n[n] = (ok && est > 0.0) ? var / (est * est) : INFINITY;
+    }
+    return ORC_OK;
+}

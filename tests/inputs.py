@@ -1,0 +1,71 @@
+"""Seeded synthetic inputs shared by the oracle tests and the GPU parity tests.
+
+Holds none of the method's arithmetic: no weights, ratios, decisions or
+random-number mapping -- only random self-avoiding walk snapshots (grown by
+picking uniformly among unvisited neighbours and restarting when stuck) and
+random scalar states in the ranges the method meets.
+"""
+import numpy as np
+
+# unit steps in the order +x, -x, +y, -y, +z, -z
+STEPS = {
+    2: np.array([[1, 0], [-1, 0], [0, 1], [0, -1]], dtype=np.int64),
+    3: np.array([[1, 0, 0], [-1, 0, 0], [0, 1, 0], [0, -1, 0], [0, 0, 1], [0, 0, -1]],
+                dtype=np.int64),
+}
+
+
+def random_saw(rng, d, n, max_restarts=100000):
+    """A random n-step self-avoiding walk from the origin, shape (n+1, d)."""
+    steps = STEPS[d]
+    for _ in range(max_restarts):
+        walk = [tuple([0] * d)]
+        seen = {walk[0]}
+        ok = True
+        for _k in range(n):
+            cur = np.array(walk[-1])
+            cand = [tuple(cur + s) for s in steps]
+            cand = [p for p in cand if p not in seen]
+            if not cand:
+                ok = False
+                break
+            p = cand[rng.integers(len(cand))]
+            walk.append(p)
+            seen.add(p)
+        if ok:
+            return np.array(walk, dtype=np.int32)
+    raise RuntimeError("no walk found")
+
+
+def free_neighbours(walk):
+    """Directions (indices into STEPS) whose target site is not on the walk."""
+    d = walk.shape[1]
+    seen = {tuple(p) for p in walk.tolist()}
+    end = walk[-1].astype(np.int64)
+    return [j for j, s in enumerate(STEPS[d]) if tuple((end + s).tolist()) not in seen]
+
+
+def random_state(rng, n):
+    """Scalar state of a node: weight W, running average T (before W), tours M,
+    DFS ordinal, sequence and tour indices."""
+    W = float(10.0 ** rng.uniform(-3, 3))
+    # T spans both r < 1 and r > 1; sometimes exactly zero (first visit)
+    T = 0.0 if rng.random() < 0.05 else float(W * 10.0 ** rng.uniform(-1.5, 1.5))
+    M = int(rng.integers(1, 1 << 20))
+    ordinal = int(rng.integers(0, 1 << 40))
+    seq = int(rng.integers(0, 1 << 16))
+    tour = int(rng.integers(0, 1 << 20))
+    return dict(W=W, T=T, M=M, ordinal=ordinal, seq=seq, tour=tour)
+
+
+def snapshot_batch(seed, d, n_max, count, n_lo=0):
+    """count random snapshot states with walks of length in [n_lo, n_max]."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for _ in range(count):
+        n = int(rng.integers(n_lo, n_max + 1))
+        walk = random_saw(rng, d, n)
+        st = random_state(rng, n)
+        st["walk"] = walk
+        out.append(st)
+    return out

@@ -1,0 +1,154 @@
+"""The oracle's pins are sensitive: plant plausible mistakes in a temporary copy
+of the oracle source (on the CPU only), rebuild it, and check that at least one
+pin fails for every mistake while all of them hold for the real source."""
+import ctypes
+import math
+import os
+import subprocess
+import tempfile
+
+import numpy as np
+import pytest
+
+from oracle import oracle as orc
+from tests import inputs
+from tests.conftest import load_counts
+
+SRC = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))),
+                   "oracle", "perm_oracle.c")
+
+MUTATIONS = {
+    "child weight misses a_+": ("o->child_w = ldexp(Wp * (double)a, -dE);",
+                                "o->child_w = ldexp(Wp, -dE);"),
+    "copies keep full weight": ("Wp = W / (double)c;", "Wp = W;"),
+    "survivor not reweighted": ("Wp = (W * 4294967296.0) / (double)K;", "Wp = W;"),
+    "own weight left out of r": ("float x = rho + invM;", "float x = rho;"),
+    "M off by one": ("double T = Wn[n] / (double)M;", "double T = Wn[n] / (double)(M + 1);"),
+    "rounding probability inverted": ("float c_raw = ((uint64_t)w[0] < Kp) ? fl : ce;",
+                                      "float c_raw = ((uint64_t)w[0] < Kp) ? ce : fl;"),
+    "Fisher-Yates offset dropped": ("int j = i + (int)(prod >> 32);", "int j = (int)(prod >> 32);"),
+    "backtrack leaves a site": ("for (int k = n; k > dp; --k) occ_set",
+                                "for (int k = n; k > dp + 1; --k) occ_set"),
+    "variance from X not X^2": ("Qn[k] += h->X[k] * h->X[k];", "Qn[k] += h->X[k];"),
+    "direction signs swapped": ("to[j >> 1] += (j & 1) ? -1 : 1;", "to[j >> 1] += (j & 1) ? 1 : -1;"),
+    "scale step wrong": ("int dE = orc_scale_exp(d, n + 1) - orc_scale_exp(d, n);",
+                         "int dE = orc_scale_exp(d, n + 1);"),
+    "tour sum counts visits": ("h->X[n] += W;", "h->X[n] += 1.0;"),
+    "root ratio not forced": ("if (n == 0) return 1.0f;", "if (n < 0) return 1.0f;"),
+    "Philox round permutation": ("uint32_t y0 = hi1 ^ x1 ^ k0;", "uint32_t y0 = hi0 ^ x1 ^ k0;"),
+}
+
+
+def _pins_hold(exact2):
+    """A quick subset of tests/test_oracle_pins.py; False at the first failure."""
+    # Philox known answer
+    if list(orc.philox4x32_10([0, 0, 0, 0], [0, 0])) != [0x6627E8D5, 0xE169C58D, 0xBC57AC4C, 0x9B00DBD8]:
+        return False
+    # a_+ and free mask against an independent neighbour check
+    for st in inputs.snapshot_batch(4, 2, 20, 60, n_lo=1):
+        out = orc.step(2, 30, st["walk"], st["W"], st["T"], st["M"], st["ordinal"],
+                       st["seq"], st["tour"], seed=5)
+        free = inputs.free_neighbours(st["walk"])
+        if out["free_mask"] != sum(1 << j for j in free):
+            return False
+    # exact short lengths and first-tour chain
+    h = orc.Oracle(2, 12, 3, seed=17)
+    h.run(200)
+    lc, S, rv = h.estimates()
+    for n, c in enumerate([1, 4, 12, 36]):
+        if not math.isclose(math.exp(lc[n]), c, rel_tol=1e-12):
+            return False
+    h1 = orc.Oracle(2, 20, 1, seed=3)
+    h1.run(1)
+    if h1.tables()["max_stack"] != 0:
+        return False
+    # probabilities of enrichment and survival (Sec. 2)
+    walk = np.array([[0, 0], [1, 0], [1, 1]], dtype=np.int32)
+    for target in (2.3, 0.37):
+        M = 1 << 30
+        T = 1.0 / target - 1.0 / M
+        r = float(orc.ratio(2, 1.0, T, M))
+        hits = 0
+        trials = 6000
+        for k in range(trials):
+            out = orc.step(2, 10, walk, 1.0, T, M, k, 1, 2, seed=99)
+            if target > 1:
+                hits += out["c"] == 2
+            else:
+                hits += out["outcome"] == 3
+        p = (math.ceil(r) - r) if target > 1 else r
+        if abs(hits / trials - p) > 5 * math.sqrt(p * (1 - p) / trials):
+            return False
+    # r = 1 at the empty walk whatever the table says (one child per tour)
+    if orc.ratio(0, 3.0, 100.0, 7) != 1.0:
+        return False
+    # ordered pairs of distinct steps (c = 2 of three free steps) are uniform
+    pairs = {}
+    for k in range(6000):
+        out = orc.step(2, 10, np.array([[0, 0], [1, 0]], dtype=np.int32), 1.0,
+                       0.5 - 1.0 / (1 << 30), 1 << 30, k, 0, 0, seed=11)
+        pairs[tuple(out["dirs"])] = pairs.get(tuple(out["dirs"]), 0) + 1
+    if len(pairs) != 6 or sum((v - 1000.0) ** 2 / 1000.0 for v in pairs.values()) > 5 + 6 * math.sqrt(10):
+        return False
+    # direction uniformity with c = 1 (three free steps)
+    counts = np.zeros(4)
+    for k in range(6000):
+        out = orc.step(2, 10, np.array([[0, 0], [1, 0]], dtype=np.int32), 1.0,
+                       1.0 - 1.0 / (1 << 30), 1 << 30, k, 0, 0, seed=7)
+        counts[out["dirs"][0]] += 1
+    exp_ = 2000.0
+    if counts[1] != 0 or sum((counts[[0, 2, 3]] - exp_) ** 2 / exp_) > 2 + 6 * 2:
+        return False
+    # counting theorem within 4 sigma, finite variance
+    h = orc.Oracle(2, 12, 8, seed=1)
+    h.run(1500)
+    lc, S, rv = h.estimates()
+    ex = np.array(exact2[:13], dtype=float)
+    with np.errstate(divide="ignore", invalid="ignore"):
+        z = (np.exp(lc - np.log(ex)) - 1.0) / np.sqrt(rv)
+    zz = z[4:]
+    if not (np.all(np.isfinite(zz)) and np.max(np.abs(zz)) < 4.0):
+        return False
+    # variance calibration, coarse: spread of z over seeds is O(1)
+    zs = []
+    for s in range(12):
+        h = orc.Oracle(2, 10, 2, seed=500 + s)
+        h.run(800)
+        lc, S, rv = h.estimates()
+        with np.errstate(divide="ignore", invalid="ignore"):
+            zs.append((math.exp(lc[10] - math.log(exact2[10])) - 1.0) / math.sqrt(rv[10]))
+    sd = float(np.std(zs))
+    if not (0.4 < sd < 2.5):
+        return False
+    return True
+
+
+def _build_variant(src_text, tmpdir, name):
+    c_path = os.path.join(tmpdir, name + ".c")
+    so_path = os.path.join(tmpdir, name + ".so")
+    with open(c_path, "w") as f:
+        f.write(src_text)
+    inc = os.path.dirname(SRC)
+    subprocess.run(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-ffp-contract=off",
+                    "-I", inc, "-o", so_path, c_path, "-lm"], check=True)
+    return so_path
+
+
+def test_pins_detect_planted_mistakes():
+    exact2 = load_counts(2)
+    src = open(SRC).read()
+    saved = orc._lib
+    survivors = []
+    try:
+        with tempfile.TemporaryDirectory() as tmp:
+            orc._lib = orc.configure(ctypes.CDLL(_build_variant(src, tmp, "orig")))
+            assert _pins_hold(exact2), "pins must hold for the unmodified oracle"
+            for i, (label, (old, new)) in enumerate(MUTATIONS.items()):
+                assert src.count(old) == 1, label
+                so = _build_variant(src.replace(old, new), tmp, "mut%d" % i)
+                orc._lib = orc.configure(ctypes.CDLL(so))
+                if _pins_hold(exact2):
+                    survivors.append(label)
+    finally:
+        orc._lib = saved
+    assert not survivors, "mistakes the pins did not catch: %s" % survivors
