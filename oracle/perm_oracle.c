@@ -36,7 +36,9 @@
  *  - r is 1 at the empty walk, so every tour has exactly one node of length 0
  *    and one of length 1.
  *  - r is evaluated in single precision by the recipe in orc_ratio (the
- *    decision precision of the GPU kernel); weights stay in double precision.
+ *    decision precision of the GPU kernel; mantissas are rounded to nearest,
+ *    so that values within an ulp of each other give the same r except next
+ *    to a rounding midpoint); weights stay in double precision.
  *  - Enriched copies take distinct steps, c is capped at a_+, each child has
  *    weight (W/c).a_+.  Survival after pruning has probability q = K/2^32 with
  *    K = ceil(r 2^32), and the survivor carries W/q (so the estimator stays
@@ -136,8 +138,22 @@ int orc_enumerate(int d, int n, int64_t *c_out) {
 /* ------------------------------------------------------------------------- */
 int orc_scale_exp(int d, int n) { return d == 2 ? (11 * n) / 8 : (9 * n) / 4; }
 
-/* a/b for finite a >= 0, b > 0 in single precision: both mantissas are cut to
- * 24 bits, divided in FP32 (round to nearest), and the exponent difference
+/* Mantissa of a positive normal double rounded to 24 bits (nearest, ties to
+ * even) as a float in [1, 2), with the exponent adjusted for a carry. */
+static float mant24(uint64_t bits, int *ef) {
+    uint64_t frac = bits & 0xFFFFFFFFFFFFFull;
+    uint32_t keep = (uint32_t)(frac >> 29);
+    uint64_t rem = frac & 0x1FFFFFFFull, half = 0x10000000ull;
+    if (rem > half || (rem == half && (keep & 1u))) keep += 1u;
+    if (keep == (1u << 23)) { keep = 0u; *ef += 1; }
+    uint32_t fb = (127u << 23) | keep;
+    float f;
+    memcpy(&f, &fb, 4);
+    return f;
+}
+
+/* a/b for finite a >= 0, b > 0 in single precision: both mantissas are rounded
+ * to 24 bits, divided in FP32 (round to nearest), and the exponent difference
  * (clamped to [-100, 100]) is applied exactly. */
 static float ratio_f32(double a, double b) {
     uint64_t ab, bb;
@@ -146,11 +162,7 @@ static float ratio_f32(double a, double b) {
     int ea_f = (int)((ab >> 52) & 0x7FF), eb_f = (int)((bb >> 52) & 0x7FF);
     if (ea_f == 0) return 0.0f;                        /* a zero (or subnormal) */
     if (eb_f == 0) return 1.2676506e30f;               /* 2^100: b zero or subnormal */
-    uint32_t fa_bits = (127u << 23) | (uint32_t)((ab & 0xFFFFFFFFFFFFFull) >> 29);
-    uint32_t fb_bits = (127u << 23) | (uint32_t)((bb & 0xFFFFFFFFFFFFFull) >> 29);
-    float fa, fb;
-    memcpy(&fa, &fa_bits, 4);
-    memcpy(&fb, &fb_bits, 4);
+    float fa = mant24(ab, &ea_f), fb = mant24(bb, &eb_f);
     float q = fa / fb;                                 /* in (0.5, 2) */
     int e = ea_f - eb_f;
     if (e > 100) e = 100;

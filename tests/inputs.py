@@ -69,3 +69,33 @@ def snapshot_batch(seed, d, n_max, count, n_lo=0):
         st["walk"] = walk
         out.append(st)
     return out
+
+
+def shortest_trapped_walk_2d(max_len=8):
+    """A shortest square-lattice walk whose end-point has no free neighbour
+    (iterative-deepening search), shape (n+1, 2)."""
+    steps = STEPS[2]
+
+    def search(walk, seen, depth):
+        end = walk[-1]
+        nbrs = [(end[0] + int(s[0]), end[1] + int(s[1])) for s in steps]
+        if all(p in seen for p in nbrs):
+            return list(walk)
+        if depth == 0:
+            return None
+        for p in nbrs:
+            if p not in seen:
+                seen.add(p)
+                walk.append(p)
+                res = search(walk, seen, depth - 1)
+                walk.pop()
+                seen.discard(p)
+                if res:
+                    return res
+        return None
+
+    for limit in range(1, max_len + 1):
+        res = search([(0, 0)], {(0, 0)}, limit)
+        if res:
+            return np.array(res, dtype=np.int32)
+    return None

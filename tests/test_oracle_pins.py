@@ -127,32 +127,9 @@ def test_step_a_plus_and_distinct_free_children(d):
 
 
 def test_step_trapped_walk():
-    # find a trapped 2D walk by a small search (independent of the oracle)
-    steps = inputs.STEPS[2]
-
-    def search(walk, seen, depth):
-        end = walk[-1]
-        nbrs = [tuple(e + s for e, s in zip(end, st)) for st in steps]
-        if all(p in seen for p in nbrs):
-            return list(walk)
-        if depth == 0:
-            return None
-        for p in nbrs:
-            if p not in seen:
-                seen.add(p); walk.append(p)
-                res = search(walk, seen, depth - 1)
-                walk.pop(); seen.discard(p)
-                if res:
-                    return res
-        return None
-
-    trapped = None
-    for limit in range(1, 9):                 # iterative deepening: shortest first
-        trapped = search([(0, 0)], {(0, 0)}, limit)
-        if trapped:
-            break
+    trapped = inputs.shortest_trapped_walk_2d()     # independent geometric search
     assert trapped is not None and len(trapped) - 1 == 7   # shortest trap: 7 steps
-    out = orc.step(2, 20, np.array(trapped), 1.0, 1.0, 10, 0, 0, 0, seed=1)
+    out = orc.step(2, 20, trapped, 1.0, 1.0, 10, 0, 0, 0, seed=1)
     assert out["outcome"] == 1 and out["a_plus"] == 0
 
 
