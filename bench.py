@@ -1,0 +1,347 @@
+#!/usr/bin/env python3
+"""Benchmark: walk-growth steps/s of interacting flatPERM (Algorithm 2) on GB300.
+
+Workload (one "step" = one complete run from empty tables): square lattice,
+n_max = 512, 4096 interacting sequences x 256 tours each, shared FP64 tables,
+Philox4x32-10 seed 1 -- synthetic by construction (the lattice is the input).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line.  Under torchrun each rank runs an independent replica
+(distinct run id) on its own GPU; value = all ranks' steps / max time.
+"""
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "walk-growth steps/s and time to 1e-4 rel. error in c_n (1 GB300) vs plain form"
+UNIT = "steps/s"
+WORKLOAD = dict(d=2, n_max=512, n_seq=4096, tours=256, seed=1)
+WORKLOAD_NAME = "plain massively parallel flatPERM, d=2, n_max=512, 4096 sequences x 256 tours"
+L2_FLUSH_BYTES = 512 << 20
+
+
+def bytes_per_step(d, f):
+    """Algorithmic bytes one growth step moves: 2d probes of k-byte keys, insert and
+    LIFO delete, the site's coordinates, the W_n/S_n update and W_n read, the per-tour
+    sum read+write, and a 16-byte stack push+pop per extra copy (f per step)."""
+    k = 4
+    base = 2 * d * k + 2 * k + 4 * d + 16 + 8 + 16
+    return base + 32.0 * f
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as fh:
+            p = json.load(fh)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", "bench_clocks_%d.csv" % index)
+
+    def __enter__(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index),
+                 "--query-gpu=index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+                 "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+                 "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.fh.close()
+
+    def summary(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        try:
+            for line in open(self.path):
+                f = [x.strip() for x in line.split(",")]
+                if len(f) < 9:
+                    continue
+                try:
+                    sm.append(float(f[1]))
+                    smax.append(float(f[2]))
+                except ValueError:
+                    continue
+                for nm, v in zip(names, f[5:9]):
+                    if v.lower() == "active":
+                        reasons.add(nm)
+        except Exception:
+            pass
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def cpu_baseline(seconds=15.0):
+    """The oracle, as it stands, on the host: the first tours of the benchmark
+    workload's sequences (single thread), until `seconds` of CPU work."""
+    from oracle import oracle as orc
+    w = WORKLOAD
+    o = orc.Oracle(w["d"], w["n_max"], w["n_seq"], w["seed"])
+    t0 = time.perf_counter()
+    rounds = 0
+    while True:
+        o.run(1)           # one more tour of each of the 4096 sequences
+        rounds += 1
+        el = time.perf_counter() - t0
+        if el >= seconds:
+            break
+    steps = o.tables()["steps"]
+    return {"value": steps / el, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": "first %d tour(s) of each of the 4096 sequences of the workload "
+                      "(%d tours, %d growth steps) in %.1f s, one host thread"
+                      % (rounds, rounds * w["n_seq"], steps, el)}
+
+
+def run_reference(args):
+    world, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    from oracle import oracle as orc
+    w = WORKLOAD
+    tours_per_step = 1   # a bounded sample: one tour of each of the 4096 sequences
+    tot_steps, tot_t = 0, 0.0
+    for it in range(args.warmup + args.steps):
+        o = orc.Oracle(w["d"], w["n_max"], w["n_seq"], w["seed"])
+        t0 = time.perf_counter()
+        o.run(tours_per_step)
+        el = time.perf_counter() - t0
+        if it >= args.warmup:
+            tot_steps += o.tables()["steps"]
+            tot_t += el
+    val = tot_steps / tot_t
+    line = {"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * tot_t / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic (the lattice is the input)",
+            "config": {"workload": WORKLOAD_NAME, "sample": "each step: the first tour of each of "
+                       "the 4096 sequences, from empty tables", "cache": "host CPU"},
+            "cpu_baseline": {"value": val, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": "each step: 4096 tours (one per sequence) of the workload, "
+                                       "one host thread"},
+            "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_ours(args):
+    import torch
+    world, rank, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", init_method="env://")
+    else:
+        torch.cuda.set_device(0)
+    from paper_2002_03000_gb300 import build as pbuild
+    if rank == 0 or world == 1:
+        pbuild.build()
+    if world > 1:
+        torch.distributed.barrier()
+    import numpy as np
+    import paper_2002_03000_gb300 as pg
+    from paper_2002_03000_gb300 import _native as nat
+
+    w = WORKLOAD
+    stream = torch.cuda.Stream()
+    run = pg.Run(w["d"], w["n_max"], w["n_seq"], w["seed"], run_id=rank)
+    run.set_stream(stream.cuda_stream)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+
+    def one_step():
+        run.reset()
+        nat.perm_run(run.h, w["tours"])
+
+    for _ in range(args.warmup):
+        one_step()
+    torch.cuda.synchronize()
+    st0 = run.stats()
+
+    # ---- device-timed region: K complete runs, L2 flushed between them ----
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    kev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(args.steps)]
+    steps_total, copies_total = 0, 0
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clocks:
+        wall0 = time.perf_counter()
+        for i in range(args.steps):
+            flush.zero_()
+            torch.cuda.current_stream().synchronize()
+            with torch.cuda.stream(stream):
+                ev[i][0].record(stream)
+                run.reset()
+                kev[i][0].record(stream)
+                nat.perm_run(run.h, w["tours"])
+                kev[i][1].record(stream)
+                ev[i][1].record(stream)
+            stream.synchronize()
+            s = run.stats()
+            if s["status"] != 0:
+                raise RuntimeError("run failed: %s" % nat.strerror(s["status"]))
+            steps_total += s["steps"]
+            copies_total += s["copies"]
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - wall0
+    if world > 1:
+        torch.distributed.barrier()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    kern_ms = [a.elapsed_time(b) for a, b in kev]
+    t_dev = sum(step_ms) / 1000.0
+    # max over ranks of the device time; sum of steps over ranks
+    if world > 1:
+        tt = torch.tensor([t_dev, float(steps_total)], dtype=torch.float64, device="cuda")
+        mx = tt.clone()
+        torch.distributed.all_reduce(mx[:1], op=torch.distributed.ReduceOp.MAX)
+        torch.distributed.all_reduce(tt[1:], op=torch.distributed.ReduceOp.SUM)
+        t_dev, steps_all = float(mx[0]), float(tt[1])
+    else:
+        steps_all = float(steps_total)
+    value = steps_all / t_dev
+
+    # ---- end to end through the C ABI, host buffers: run + estimates to host ----
+    L = w["n_max"] + 1
+    lc, S, rv = np.empty(L), np.empty(L), np.empty(L)
+    e2e_steps = 0
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for i in range(args.steps):
+        nat.perm_reset(run.h)
+        nat.perm_run(run.h, w["tours"])
+        lc, S, rv = nat.perm_estimates(run.h, w["n_max"])
+        e2e_steps += run.stats()["steps"]
+    e2e_t = time.perf_counter() - t0
+    if world > 1:
+        tt = torch.tensor([e2e_t, float(e2e_steps)], dtype=torch.float64, device="cuda")
+        mx = tt.clone()
+        torch.distributed.all_reduce(mx[:1], op=torch.distributed.ReduceOp.MAX)
+        torch.distributed.all_reduce(tt[1:], op=torch.distributed.ReduceOp.SUM)
+        e2e_t, e2e_steps = float(mx[0]), float(tt[1])
+    e2e_value = e2e_steps / e2e_t
+    d2h = 3 * L * 8 + 4 + 8 * 3 + 8   # W_n, S_n, Q_n tables, status, counters, M
+
+    # ---- time to 1e-4 relative standard error of c_{n_max}, continuing one run ----
+    ttt = None
+    if rank == 0 and not args.skip_time_to_target:
+        run.reset()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        rel = float("inf")
+        chunks = 0
+        while time.perf_counter() - t0 < args.target_cap_s:
+            nat.perm_run(run.h, w["tours"])
+            chunks += 1
+            lc_t, S_t, rv_t = nat.perm_estimates(run.h, w["n_max"])
+            rel = math.sqrt(rv_t[w["n_max"]])
+            if rel <= 1e-4:
+                break
+        el = time.perf_counter() - t0
+        ttt = {"target_rel_se_c_nmax": 1e-4, "reached": rel <= 1e-4, "seconds": el,
+               "rel_se": rel, "tours_per_seq": chunks * w["tours"],
+               "note": "one run continued in chunks of 256 tours/sequence; relative standard "
+                       "error of c_512 from the per-tour variance"}
+
+    f = copies_total / max(steps_total, 1)
+    B = bytes_per_step(w["d"], f)
+    avg_kern_s = sum(kern_ms) / len(kern_ms) / 1000.0
+    steps_per_launch = steps_total / args.steps
+    peak, peak_kind = measured_peaks()
+    achieved = B * steps_per_launch / avg_kern_s / 1e9
+    clk = clocks.summary()
+    if rank != 0:
+        run.close()
+        if world > 1:
+            torch.distributed.destroy_process_group()
+        return 0
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1000.0 * t_dev / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64", "data": "synthetic (the lattice is the input)",
+        "config": {"workload": WORKLOAD_NAME, "d": w["d"], "n_max": w["n_max"],
+                   "sequences": w["n_seq"], "tours_per_seq": w["tours"], "seed": w["seed"],
+                   "parallelism": "replicas" if world > 1 else "single GPU",
+                   "l2": "flushed between timed steps (%d MiB write)" % (L2_FLUSH_BYTES >> 20),
+                   "step": "one complete run from empty tables"},
+        "gpu_launches": 2 * args.steps,
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": d2h},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": None,
+                     "peak_source": peak_kind, "bytes_per_step": B, "copies_per_step": f,
+                     "kernel_ms": avg_kern_s * 1000.0},
+        "clocks": clk,
+        "wall_s_timed": wall,
+        "time_to_target": ttt,
+        "estimates": {"log_c_nmax": float(lc[w["n_max"]]), "rel_se_c_nmax": float(math.sqrt(rv[w["n_max"]])),
+                      "log_c_nmax_over_nmax": float(lc[w["n_max"]] / w["n_max"])},
+    }
+    if world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(args.cpu_seconds)
+    print(json.dumps(line), flush=True)
+    run.close()
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--skip-time-to-target", action="store_true")
+    ap.add_argument("--target-cap-s", type=float, default=60.0)
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,173 @@
+/*
+ * perm.h -- C ABI of the GB300 interacting-flatPERM library (libperm.so).
+ *
+ * The library runs the growth step of parallel flatPERM (Campbell and Janse
+ * van Rensburg, "Parallel PERM") for self-avoiding walks on Z^d, d = 2, 3, on
+ * one NVIDIA GB300 (sm_103a):
+ *   - Sec. 1, eqs. (1)-(2): Rosenbluth growth -- a_+ free neighbours of the
+ *     end-point, a step chosen uniformly among them, weight W = prod a_+;
+ *   - Sec. 1, eq. (4): the sample average <W_n> = sum W_n / M estimates c_n,
+ *     M being the number of tours started (passes through the empty walk);
+ *   - Sec. 2, eq. (6) and the paragraphs after it: flatPERM ratio
+ *     r = W / [W_n]^sample (own weight included), enrichment into c copies of
+ *     weight W/c (c = floor r with probability ceil r - r, else ceil r),
+ *     pruning with probability 1 - r and survival with weight W/r;
+ *   - Sec. 3, Algorithm 2 and Fig. 1: N sequences grow concurrently and share
+ *     one table W; Algorithm 1: N sequences with private tables.
+ *
+ * Conventions (every entry point):
+ *   - Return PERM_OK (0) on success or a negative PERM_E* code; perm_strerror
+ *     names it.  No entry point aborts or traps; a failure inside a kernel is
+ *     reported through the handle's status word as PERM_EOVERFLOW/PERM_EDEVICE.
+ *   - The library owns all device memory it allocates; the caller owns every
+ *     host array it passes, and every device pointer passed to
+ *     perm_debug_step.  Host arrays of length n_max+1 are indexed by n.
+ *   - A handle is not thread safe.  Work is queued on the handle's CUDA stream
+ *     (perm_set_stream; default: a stream the library creates).
+ */
+#ifndef PERM_H
+#define PERM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define PERM_OK 0
+#define PERM_EINVAL (-1)     /* bad argument (d, n_max, n_seq, pointer, mode) */
+#define PERM_ENOMEM (-2)     /* device or host allocation failed */
+#define PERM_EOVERFLOW (-3)  /* a kernel found a stack or hash bound exceeded; run invalid */
+#define PERM_EDEVICE (-4)    /* CUDA error (launch, copy, no device) */
+#define PERM_ETIMEOUT (-5)   /* a bounded device wait ran out; run invalid */
+#define PERM_EUNSUPPORTED (-6) /* configuration this build does not handle */
+
+typedef struct perm_run_s *perm_handle;
+
+/* Algorithms (Sec. 3, Fig. 1). */
+#define PERM_ALG2 2   /* N interacting sequences, one shared table W (default) */
+#define PERM_ALG1 1   /* N independent sequences, one table each */
+
+/* Where a node reads its threshold [W_n]^sample from (Algorithm 2). */
+#define PERM_THRESH_SNAPSHOT 0  /* per-SM copy of W_n/M, refreshed every refresh_ns (default) */
+#define PERM_THRESH_FRESH 1     /* global table read by the node's own atomic add (exact
+                                   sequential flatPERM when N = 1) */
+
+typedef struct {
+    int d;             /* lattice dimension, 2 or 3 */
+    int n_max;         /* longest walk length; 1..32766 (d=2), 1..1048574 (d=3) */
+    int n_seq;         /* N, number of flatPERM sequences, >= 1 */
+    uint64_t seed;     /* Philox key material */
+    uint32_t run_id;   /* XORed into the low key word (distinct runs, one seed) */
+    int alg;           /* PERM_ALG2 or PERM_ALG1 */
+    int threshold;     /* PERM_THRESH_SNAPSHOT or PERM_THRESH_FRESH (Alg. 2 only) */
+    int slots;         /* concurrent walks on the GPU; 0 = min(N, device capacity) */
+    int lanes_per_warp;/* walks per warp, 1..32; 0 = as many as fit (up to 32) */
+    int refresh_ns;    /* snapshot refresh period in ns; 0 = default (4000) */
+    double max_seconds;/* wall-clock bound of one launch; past it the kernel stops and the
+                          run reports PERM_ETIMEOUT; 0 = default (600) */
+} perm_config;
+
+/* Fill cfg with defaults for (d, n_max, n_seq, seed). */
+void perm_config_init(perm_config *cfg, int d, int n_max, int n_seq, uint64_t seed);
+
+/* Create a run with default settings (Algorithm 2, snapshot thresholds).
+ * out: receives the handle (NULL on failure).  Allocates the shared tables
+ * W_n, S_n, Q_n (FP64/u64, n_max+1 each), the tour counter M and per-walk
+ * scratch (tour sums, stacks) in device memory. */
+int perm_create(perm_handle *out, int d, int n_max, int n_seq, uint64_t seed);
+/* Same with every setting explicit. */
+int perm_create_ex(perm_handle *out, const perm_config *cfg);
+
+/* Queue all later work of h on `stream` (a cudaStream_t; NULL = legacy default). */
+int perm_set_stream(perm_handle h, void *stream);
+
+/* Grow tours_per_seq more tours of every sequence (cumulative: repeated calls
+ * continue the same tables, tour counters and random streams).  Queues one
+ * persistent kernel launch and returns without waiting unless `sync` is set
+ * by perm_run_sync. */
+int perm_run(perm_handle h, int64_t tours_per_seq);
+/* perm_run, then wait for the stream and report any device-side status. */
+int perm_run_sync(perm_handle h, int64_t tours_per_seq);
+
+/* Start the run over: zero the tables, the tour counters and the statistics
+ * (queued on the stream; the next perm_run begins at M = 0 with the same
+ * random streams as a fresh handle). */
+int perm_reset(perm_handle h);
+
+/* Estimates after waiting for the stream (Sec. 1, eq. 4; Alg. 1: eq. 7):
+ *   log_cn[n]   = log <W_n>, the natural log of the estimate of c_n
+ *                 (-inf where no walk reached n);
+ *   S_n[n]      = number of nodes of length n grown (histogram, as double);
+ *   relvar_n[n] = estimated variance of <W_n> divided by <W_n>^2, from the
+ *                 per-tour sums (variance = (Q_n/M - <W_n>^2)/(M-1)).
+ * Any pointer may be NULL.  Arrays have n_max+1 entries. */
+int perm_estimates(perm_handle h, double *log_cn, double *S_n, double *relvar_n);
+
+/* Raw tables after waiting: W_n, S_n, Q_n at the stored scale (the weight of a
+ * walk of length n is stored divided by 2^E(n), E(n) = floor(11n/8) for d=2,
+ * floor(9n/4) for d=3), and M.  Alg. 1 returns n_seq rows of n_max+1 and one
+ * M per sequence.  Any pointer may be NULL. */
+int perm_tables(perm_handle h, double *W_n, double *S_n, double *Q_n, int64_t *M);
+
+typedef struct {
+    int64_t steps;        /* nodes processed (walk-growth steps), cumulative */
+    int64_t tours;        /* tours started, cumulative */
+    int64_t max_stack;    /* deepest per-walk stack of waiting copies seen */
+    int64_t copies;       /* extra copies pushed by enrichment (c - 1 per node), cumulative */
+    int64_t refreshes;    /* threshold refreshes summed over CTAs, cumulative */
+    int slots, ctas, lanes_per_warp, warps_per_cta;
+    int hash_slots;       /* per-walk occupancy hash size */
+    int status;           /* PERM_OK or the device-side error of the last run */
+    int64_t device_bytes; /* device memory held by the handle */
+} perm_stats_t;
+int perm_stats(perm_handle h, perm_stats_t *out);
+
+/* Sampled node trace (test support): every node whose DFS ordinal is a
+ * multiple of `every`, in tours whose index within their sequence is a
+ * multiple of `tour_every`, is recorded, up to `capacity` records, during later perm_run calls.
+ * every = 0 switches tracing off.  perm_trace_read copies the records out
+ * (see the layout in perm_trace_record). */
+typedef struct {
+    int32_t n, a_plus, free_mask, c, outcome, pad;
+    int32_t dirs[6];
+    float r;
+    uint32_t seq, tour;
+    uint32_t pad2;
+    uint64_t ordinal, M, survive_K;
+    double W, T, child_w;
+} perm_trace_record;
+int perm_trace_enable(perm_handle h, int64_t every, int64_t tour_every, int capacity);
+/* count: records written (may exceed capacity; only capacity are kept).
+ * recs: host array of `capacity` records; coords: host int32 array of
+ * capacity*(n_max+1)*d, the walk of each record (site k at [k*d..k*d+d-1]). */
+int perm_trace_read(perm_handle h, int64_t *count, perm_trace_record *recs, int32_t *coords);
+
+void perm_destroy(perm_handle h);   /* NULL-safe; waits for the stream */
+const char *perm_strerror(int code);
+
+/* One growth step on B snapshot states (test support for step parity).
+ * All arrays are DEVICE pointers owned by the caller:
+ *   coords[B*(n_max+1)*d] int32  walk b: site k at (b*(n_max+1)+k)*d, origin first
+ *   len[B]      int32   n, the length of walk b (0..n_max)
+ *   W[B], T[B]  double  node weight and running average before it (stored scale)
+ *   M[B]        uint64  tours started
+ *   ordinal[B]  uint64  DFS ordinal of the node; seq[B], tour[B] uint32
+ *   out_i[B*10] int32   outcome, a_plus, free_mask, c, dirs[0..5]
+ *   out_r[B]    float   r;  out_w[B] double child weight;  out_K[B] uint64
+ * Outcomes: 0 walk at n_max, 1 trapped, 2 pruned, 3 children.
+ * Requires d in {2,3} and n_max <= 512.  Queued on `stream`, not waited for. */
+int perm_debug_step(int d, int n_max, int B, const int32_t *coords, const int32_t *len,
+                    const double *W, const double *T, const uint64_t *M,
+                    const uint64_t *ordinal, const uint32_t *seq, const uint32_t *tour,
+                    uint64_t seed, uint32_t run_id, int32_t *out_i, float *out_r,
+                    double *out_w, uint64_t *out_K, void *stream);
+
+/* Philox4x32-10 on the device for B counters (test support).  ctr[B*4],
+ * key[2] on the host, out[B*4]; ctr and out are DEVICE pointers.  Waits. */
+int perm_debug_philox(int B, const uint32_t *ctr, const uint32_t *key, uint32_t *out);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,73 @@
+"""GB300-native interacting flatPERM (Campbell and Janse van Rensburg, "Parallel PERM").
+
+The growth step runs in the CUDA kernels of ``csrc/`` behind the C ABI of
+``include/perm.h`` (libperm.so).  ``_native`` binds that ABI with the same
+names; ``Run`` is a small convenience wrapper around one handle.
+"""
+from . import _native
+from ._native import (PERM_ALG1, PERM_ALG2, PERM_THRESH_FRESH, PERM_THRESH_SNAPSHOT,  # noqa: F401
+                      PermError, perm_config_init)
+
+
+class Run:
+    """One flatPERM run (a perm_handle): create, run tours, read estimates."""
+
+    def __init__(self, d, n_max, n_seq, seed, run_id=0, alg=PERM_ALG2,
+                 threshold=PERM_THRESH_SNAPSHOT, slots=0, lanes_per_warp=0, refresh_ns=0,
+                 max_seconds=0.0):
+        cfg = _native.perm_config_init(d, n_max, n_seq, seed)
+        cfg.run_id = run_id
+        cfg.alg = alg
+        cfg.threshold = threshold
+        cfg.slots = slots
+        cfg.lanes_per_warp = lanes_per_warp
+        cfg.refresh_ns = refresh_ns
+        cfg.max_seconds = max_seconds
+        self.d, self.n_max, self.n_seq, self.alg = d, n_max, n_seq, alg
+        self.h = _native.perm_create_ex(cfg)
+
+    def run(self, tours_per_seq, sync=True):
+        if sync:
+            _native.perm_run_sync(self.h, tours_per_seq)
+        else:
+            _native.perm_run(self.h, tours_per_seq)
+
+    def reset(self):
+        _native.perm_reset(self.h)
+
+    def set_stream(self, stream_ptr):
+        _native.perm_set_stream(self.h, stream_ptr)
+
+    def estimates(self):
+        return _native.perm_estimates(self.h, self.n_max)
+
+    def tables(self):
+        rows = self.n_seq if self.alg == PERM_ALG1 else 1
+        return _native.perm_tables(self.h, self.n_max, rows)
+
+    def stats(self):
+        return _native.perm_stats(self.h)
+
+    def trace_enable(self, every, tour_every=1, capacity=1024):
+        self._trace_cap = capacity
+        _native.perm_trace_enable(self.h, every, tour_every, capacity)
+
+    def trace_read(self):
+        return _native.perm_trace_read(self.h, self._trace_cap, self.n_max, self.d)
+
+    def close(self):
+        if self.h:
+            _native.perm_destroy(self.h)
+            self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

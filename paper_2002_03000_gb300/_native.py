@@ -1,0 +1,210 @@
+"""ctypes binding of libperm.so: the C ABI of include/perm.h, same names.
+
+Argument marshalling only -- every step of the growth path runs in the CUDA
+kernels of csrc/.  Loading fails loudly when the library is missing or the
+device cannot run it; there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libperm.so")
+
+PERM_OK = 0
+PERM_EINVAL = -1
+PERM_ENOMEM = -2
+PERM_EOVERFLOW = -3
+PERM_EDEVICE = -4
+PERM_ETIMEOUT = -5
+PERM_EUNSUPPORTED = -6
+PERM_ALG1 = 1
+PERM_ALG2 = 2
+PERM_THRESH_SNAPSHOT = 0
+PERM_THRESH_FRESH = 1
+
+# every exported symbol declared in include/perm.h
+EXPORTS = (
+    "perm_config_init", "perm_create", "perm_create_ex", "perm_set_stream", "perm_run", "perm_reset",
+    "perm_run_sync", "perm_estimates", "perm_tables", "perm_stats", "perm_trace_enable",
+    "perm_trace_read", "perm_destroy", "perm_strerror", "perm_debug_step", "perm_debug_philox",
+)
+
+
+class perm_config(C.Structure):
+    _fields_ = [("d", C.c_int), ("n_max", C.c_int), ("n_seq", C.c_int), ("seed", C.c_uint64),
+                ("run_id", C.c_uint32), ("alg", C.c_int), ("threshold", C.c_int),
+                ("slots", C.c_int), ("lanes_per_warp", C.c_int), ("refresh_ns", C.c_int),
+                ("max_seconds", C.c_double)]
+
+
+class perm_stats_t(C.Structure):
+    _fields_ = [("steps", C.c_int64), ("tours", C.c_int64), ("max_stack", C.c_int64),
+                ("copies", C.c_int64), ("refreshes", C.c_int64),
+                ("slots", C.c_int), ("ctas", C.c_int), ("lanes_per_warp", C.c_int),
+                ("warps_per_cta", C.c_int), ("hash_slots", C.c_int), ("status", C.c_int),
+                ("device_bytes", C.c_int64)]
+
+
+class perm_trace_record(C.Structure):
+    _fields_ = [("n", C.c_int32), ("a_plus", C.c_int32), ("free_mask", C.c_int32),
+                ("c", C.c_int32), ("outcome", C.c_int32), ("pad", C.c_int32),
+                ("dirs", C.c_int32 * 6), ("r", C.c_float), ("seq", C.c_uint32),
+                ("tour", C.c_uint32), ("pad2", C.c_uint32), ("ordinal", C.c_uint64),
+                ("M", C.c_uint64), ("survive_K", C.c_uint64), ("W", C.c_double),
+                ("T", C.c_double), ("child_w", C.c_double)]
+
+
+class PermError(RuntimeError):
+    def __init__(self, code, what):
+        super().__init__("%s: %s (%d)" % (what, strerror(code), code))
+        self.code = code
+
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Load libperm.so and declare the signatures (raises if it is missing)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise ImportError("libperm.so not built: run paper_2002_03000_gb300.build.build() "
+                          "(expected at %s)" % path)
+    L = C.CDLL(path)
+    vp, i64, u64, u32 = C.c_void_p, C.c_int64, C.c_uint64, C.c_uint32
+    hp = C.POINTER(C.c_void_p)
+    dp = C.POINTER(C.c_double)
+    L.perm_config_init.argtypes = [C.POINTER(perm_config), C.c_int, C.c_int, C.c_int, u64]
+    L.perm_config_init.restype = None
+    L.perm_create.argtypes = [hp, C.c_int, C.c_int, C.c_int, u64]
+    L.perm_create_ex.argtypes = [hp, C.POINTER(perm_config)]
+    L.perm_set_stream.argtypes = [vp, vp]
+    L.perm_run.argtypes = [vp, i64]
+    L.perm_run_sync.argtypes = [vp, i64]
+    L.perm_reset.argtypes = [vp]
+    L.perm_estimates.argtypes = [vp, dp, dp, dp]
+    L.perm_tables.argtypes = [vp, dp, dp, dp, C.POINTER(i64)]
+    L.perm_stats.argtypes = [vp, C.POINTER(perm_stats_t)]
+    L.perm_trace_enable.argtypes = [vp, i64, i64, C.c_int]
+    L.perm_trace_read.argtypes = [vp, C.POINTER(i64), C.POINTER(perm_trace_record),
+                                  C.POINTER(C.c_int32)]
+    L.perm_destroy.argtypes = [vp]
+    L.perm_destroy.restype = None
+    L.perm_strerror.argtypes = [C.c_int]
+    L.perm_strerror.restype = C.c_char_p
+    L.perm_debug_step.argtypes = [C.c_int, C.c_int, C.c_int] + [vp] * 8 + [u64, u32] + [vp] * 4 + [vp]
+    L.perm_debug_philox.argtypes = [C.c_int, vp, C.POINTER(u32), vp]
+    for name in EXPORTS:
+        if name not in ("perm_config_init", "perm_destroy", "perm_strerror"):
+            getattr(L, name).restype = C.c_int
+    _lib = L
+    return L
+
+
+def strerror(code: int) -> str:
+    try:
+        return load().perm_strerror(code).decode()
+    except Exception:
+        return "error %d" % code
+
+
+def _check(code, what):
+    if code != PERM_OK:
+        raise PermError(code, what)
+
+
+def _dp(a):
+    return a.ctypes.data_as(C.POINTER(C.c_double))
+
+
+def perm_config_init(d, n_max, n_seq, seed):
+    cfg = perm_config()
+    load().perm_config_init(C.byref(cfg), d, n_max, n_seq, seed)
+    return cfg
+
+
+def perm_create(d, n_max, n_seq, seed):
+    h = C.c_void_p()
+    _check(load().perm_create(C.byref(h), d, n_max, n_seq, seed), "perm_create")
+    return h
+
+
+def perm_create_ex(cfg: perm_config):
+    h = C.c_void_p()
+    _check(load().perm_create_ex(C.byref(h), C.byref(cfg)), "perm_create_ex")
+    return h
+
+
+def perm_set_stream(h, stream_ptr: int):
+    _check(load().perm_set_stream(h, C.c_void_p(stream_ptr)), "perm_set_stream")
+
+
+def perm_run(h, tours_per_seq: int):
+    _check(load().perm_run(h, tours_per_seq), "perm_run")
+
+
+def perm_run_sync(h, tours_per_seq: int):
+    _check(load().perm_run_sync(h, tours_per_seq), "perm_run_sync")
+
+
+def perm_reset(h):
+    _check(load().perm_reset(h), "perm_reset")
+
+
+def perm_estimates(h, n_max: int):
+    L = n_max + 1
+    lc, S, rv = np.empty(L), np.empty(L), np.empty(L)
+    _check(load().perm_estimates(h, _dp(lc), _dp(S), _dp(rv)), "perm_estimates")
+    return lc, S, rv
+
+
+def perm_tables(h, n_max: int, rows: int = 1):
+    L = (n_max + 1) * rows
+    W, S, Q = np.empty(L), np.empty(L), np.empty(L)
+    M = np.zeros(rows, dtype=np.int64)
+    _check(load().perm_tables(h, _dp(W), _dp(S), _dp(Q), M.ctypes.data_as(C.POINTER(C.c_int64))),
+           "perm_tables")
+    return dict(W=W, S=S, Q=Q, M=M)
+
+
+def perm_stats(h) -> dict:
+    st = perm_stats_t()
+    _check(load().perm_stats(h, C.byref(st)), "perm_stats")
+    return {name: getattr(st, name) for name, _ in perm_stats_t._fields_}
+
+
+def perm_trace_enable(h, every: int, tour_every: int, capacity: int):
+    _check(load().perm_trace_enable(h, every, tour_every, capacity), "perm_trace_enable")
+
+
+def perm_trace_read(h, capacity: int, n_max: int, d: int):
+    count = C.c_int64(0)
+    recs = (perm_trace_record * max(capacity, 1))()
+    coords = np.zeros(max(capacity, 1) * (n_max + 1) * d, dtype=np.int32)
+    _check(load().perm_trace_read(h, C.byref(count), recs,
+                                  coords.ctypes.data_as(C.POINTER(C.c_int32))), "perm_trace_read")
+    kept = min(count.value, capacity)
+    return count.value, [recs[i] for i in range(kept)], coords.reshape(-1, n_max + 1, d)[:kept]
+
+
+def perm_destroy(h):
+    if h:
+        load().perm_destroy(h)
+
+
+def perm_debug_step(d, n_max, B, coords, length, W, T, M, ordinal, seq, tour, seed, run_id,
+                    out_i, out_r, out_w, out_K, stream=0):
+    """All array arguments are device pointers (ints), e.g. tensor.data_ptr()."""
+    _check(load().perm_debug_step(d, n_max, B, coords, length, W, T, M, ordinal, seq, tour,
+                                  seed, run_id, out_i, out_r, out_w, out_K, stream),
+           "perm_debug_step")
+
+
+def perm_debug_philox(B, ctr_dev, key, out_dev):
+    k = (C.c_uint32 * 2)(int(key[0]), int(key[1]))
+    _check(load().perm_debug_philox(B, ctr_dev, k, out_dev), "perm_debug_philox")

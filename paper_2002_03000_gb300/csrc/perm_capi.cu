@@ -1,0 +1,455 @@
+// perm_capi.cu -- C ABI of libperm.so (declared in include/perm.h).
+//
+// Host side of the interacting flatPERM run: argument checks, the layout of
+// walks on the device (slots per warp, warps per CTA, CTAs), device memory,
+// launches, and the estimates of Sec. 1, eq. (4) (Alg. 1: eq. (7)) computed
+// from the tables the kernels fill.
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "perm.h"
+#include "perm_kernels.cuh"
+
+using perm::RunDev;
+
+struct perm_run_s {
+    perm_config cfg;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    int device = 0, num_sms = 0;
+    bool key64 = false;
+    int thresh = perm::kSnapshot;
+    int log2h = 0, slots = 0, ctas = 0, worker_warps = 0, lanes = 0, stride = 32, stack_cache = 16;
+    size_t smem = 0;
+    int ntab = 1;
+    // device buffers
+    double *Wn = nullptr, *Qn = nullptr, *X = nullptr, *gstk_w = nullptr;
+    unsigned long long *Sn = nullptr, *tickets = nullptr, *seq_M = nullptr;
+    unsigned long long *steps = nullptr, *max_stack = nullptr, *copies = nullptr, *refreshes = nullptr, *trace_count = nullptr;
+    uint32_t *gstk_meta = nullptr;
+    int *status = nullptr;
+    perm_trace_record *trace = nullptr;
+    int32_t *trace_coords = nullptr;
+    int trace_cap = 0;
+    long long trace_every = 0, trace_tour_every = 1;
+    // host bookkeeping
+    long long tour_limit = 0;      // Alg. 2 tickets handed out so far (cumulative)
+    long long seq_target = 0;      // Alg. 1 tours per sequence (cumulative)
+    long long device_bytes = 0;
+    int last_status = PERM_OK;
+};
+
+namespace {
+
+int to_code(cudaError_t e) {
+    if (e == cudaSuccess) return PERM_OK;
+    if (e == cudaErrorMemoryAllocation) return PERM_ENOMEM;
+    return PERM_EDEVICE;
+}
+
+template <typename T>
+int dalloc(perm_handle h, T **p, size_t count) {
+    const size_t bytes = count * sizeof(T);
+    if (bytes == 0) { *p = nullptr; return PERM_OK; }
+    cudaError_t e = cudaMalloc((void **)p, bytes);
+    if (e != cudaSuccess) { *p = nullptr; return to_code(e); }
+    h->device_bytes += (long long)bytes;
+    e = cudaMemsetAsync(*p, 0, bytes, h->stream);
+    return to_code(e);
+}
+
+void free_all(perm_handle h) {
+    void *ptrs[] = {h->Wn, h->Qn, h->X, h->gstk_w, h->Sn, h->tickets, h->seq_M, h->steps,
+                    h->max_stack, h->copies, h->refreshes, h->trace_count, h->gstk_meta, h->status, h->trace,
+                    h->trace_coords};
+    for (void *p : ptrs) if (p) cudaFree(p);
+}
+
+int scale_exp_host(int d, int n) { return d == 2 ? (11 * n) >> 3 : (9 * n) >> 2; }
+
+int max_n_for(int d, bool key64) {
+    if (d == 2) return 32766;
+    return key64 ? (1 << 20) - 2 : 512;
+}
+
+}  // namespace
+
+extern "C" {
+
+void perm_config_init(perm_config *cfg, int d, int n_max, int n_seq, uint64_t seed) {
+    if (!cfg) return;
+    std::memset(cfg, 0, sizeof(*cfg));
+    cfg->d = d;
+    cfg->n_max = n_max;
+    cfg->n_seq = n_seq;
+    cfg->seed = seed;
+    cfg->run_id = 0u;
+    cfg->alg = PERM_ALG2;
+    cfg->threshold = PERM_THRESH_SNAPSHOT;
+    cfg->slots = 0;
+    cfg->lanes_per_warp = 0;
+    cfg->refresh_ns = 0;
+    cfg->max_seconds = 0.0;
+}
+
+const char *perm_strerror(int code) {
+    switch (code) {
+        case PERM_OK: return "ok";
+        case PERM_EINVAL: return "invalid argument";
+        case PERM_ENOMEM: return "out of memory";
+        case PERM_EOVERFLOW: return "stack or hash bound exceeded in a kernel";
+        case PERM_EDEVICE: return "CUDA device error";
+        case PERM_ETIMEOUT: return "bounded device wait ran out";
+        case PERM_EUNSUPPORTED: return "configuration not supported";
+        default: return "unknown error";
+    }
+}
+
+int perm_create_ex(perm_handle *out, const perm_config *cfg) {
+    if (!out || !cfg) return PERM_EINVAL;
+    *out = nullptr;
+    const int d = cfg->d, n_max = cfg->n_max, n_seq = cfg->n_seq;
+    if ((d != 2 && d != 3) || n_max < 1 || n_seq < 1) return PERM_EINVAL;
+    if (cfg->alg != PERM_ALG1 && cfg->alg != PERM_ALG2) return PERM_EINVAL;
+    if (cfg->threshold != PERM_THRESH_SNAPSHOT && cfg->threshold != PERM_THRESH_FRESH) return PERM_EINVAL;
+    if (cfg->slots < 0 || cfg->refresh_ns < 0 || !(cfg->max_seconds >= 0.0)) return PERM_EINVAL;
+    const int lpw = cfg->lanes_per_warp;
+    if (lpw != 0 && (lpw < 1 || lpw > 32)) return PERM_EINVAL;
+    const bool key64 = (d == 3 && n_max > 512);
+    if (n_max > max_n_for(d, key64)) return PERM_EUNSUPPORTED;
+
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return PERM_EDEVICE;
+    cudaDeviceProp prop;
+    if (cudaGetDeviceProperties(&prop, dev) != cudaSuccess) return PERM_EDEVICE;
+
+    perm_handle h = new (std::nothrow) perm_run_s();
+    if (!h) return PERM_ENOMEM;
+    h->cfg = *cfg;
+    if (h->cfg.refresh_ns == 0) h->cfg.refresh_ns = 4000;
+    if (h->cfg.refresh_ns > 1000000) h->cfg.refresh_ns = 1000000;
+    if (h->cfg.max_seconds == 0.0) h->cfg.max_seconds = 600.0;
+    h->device = dev;
+    h->num_sms = prop.multiProcessorCount;
+    h->key64 = key64;
+    // Algorithm 1 reads its private rows directly (no snapshot needed)
+    h->thresh = (cfg->alg == PERM_ALG1) ? perm::kFresh
+              : (cfg->threshold == PERM_THRESH_FRESH ? perm::kFresh : perm::kSnapshot);
+    int log2h = 4;
+    while ((1 << log2h) < 2 * n_max) ++log2h;
+    h->log2h = log2h;
+    if (cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking) != cudaSuccess) {
+        delete h;
+        return PERM_EDEVICE;
+    }
+    h->own_stream = true;
+
+    // layout: interleave stride (walks per warp), worker warps per CTA, CTAs
+    const bool snap = (h->thresh == perm::kSnapshot);
+    const size_t budget = prop.sharedMemPerBlockOptin;
+    int stride = 32;
+    while (lpw && stride / 2 >= lpw) stride /= 2;
+    size_t head = 0, per_warp = 0;
+    for (;; stride /= 2) {
+        head = perm::cta_smem_bytes(d, key64, n_max, log2h, h->stack_cache, 0, snap, stride);
+        per_warp = perm::cta_smem_bytes(d, key64, n_max, log2h, h->stack_cache, 1, snap, stride) - head;
+        if (head + per_warp <= budget || stride == 1) break;
+    }
+    if (head + per_warp > budget) { cudaStreamDestroy(h->stream); delete h; return PERM_EUNSUPPORTED; }
+    int max_warps = (int)((budget - head) / per_warp);
+    if (max_warps > 8) max_warps = 8;
+    const int lanes_cap = (lpw && lpw < stride) ? lpw : stride;
+    const long long capacity = (long long)h->num_sms * max_warps * lanes_cap;
+    long long slots = cfg->slots ? cfg->slots : (long long)n_seq;
+    if (slots > capacity) slots = capacity;
+    if (slots > n_seq) slots = n_seq;
+    // spread the walks evenly: as few walks per SM as the count allows
+    long long per_cta = (slots + h->num_sms - 1) / h->num_sms;
+    int warps = (int)((per_cta + lanes_cap - 1) / lanes_cap);
+    if (warps > max_warps) warps = max_warps;
+    int lanes = (int)((per_cta + warps - 1) / warps);
+    if (lanes > lanes_cap) lanes = lanes_cap;
+    const long long per_cta_eff = (long long)warps * lanes;
+    h->ctas = (int)((slots + per_cta_eff - 1) / per_cta_eff);
+    h->worker_warps = warps;
+    h->lanes = lanes;
+    h->stride = stride;
+    h->slots = (int)slots;
+    h->smem = perm::cta_smem_bytes(d, key64, n_max, log2h, h->stack_cache, warps, snap, stride);
+
+    const size_t L = (size_t)n_max + 1;
+    h->ntab = (cfg->alg == PERM_ALG1) ? n_seq : 1;
+    int rc = PERM_OK;
+    if (rc == PERM_OK) rc = dalloc(h, &h->Wn, L * h->ntab);
+    if (rc == PERM_OK) rc = dalloc(h, &h->Qn, L * h->ntab);
+    if (rc == PERM_OK) rc = dalloc(h, &h->Sn, L * h->ntab);
+    if (rc == PERM_OK) rc = dalloc(h, &h->tickets, 1);
+    if (rc == PERM_OK) rc = dalloc(h, &h->seq_M, (size_t)n_seq);
+    if (rc == PERM_OK) rc = dalloc(h, &h->X, L * (size_t)h->slots);
+    if (rc == PERM_OK) rc = dalloc(h, &h->gstk_meta, (size_t)n_max * h->slots);
+    if (rc == PERM_OK) rc = dalloc(h, &h->gstk_w, (size_t)n_max * h->slots);
+    if (rc == PERM_OK) rc = dalloc(h, &h->steps, 1);
+    if (rc == PERM_OK) rc = dalloc(h, &h->max_stack, 1);
+    if (rc == PERM_OK) rc = dalloc(h, &h->copies, 1);
+    if (rc == PERM_OK) rc = dalloc(h, &h->refreshes, 1);
+    if (rc == PERM_OK) rc = dalloc(h, &h->trace_count, 1);
+    if (rc == PERM_OK) rc = dalloc(h, &h->status, 1);
+    if (rc == PERM_OK) rc = to_code(cudaStreamSynchronize(h->stream));
+    if (rc != PERM_OK) {
+        free_all(h);
+        cudaStreamDestroy(h->stream);
+        delete h;
+        return rc;
+    }
+    *out = h;
+    return PERM_OK;
+}
+
+int perm_create(perm_handle *out, int d, int n_max, int n_seq, uint64_t seed) {
+    perm_config cfg;
+    perm_config_init(&cfg, d, n_max, n_seq, seed);
+    return perm_create_ex(out, &cfg);
+}
+
+int perm_set_stream(perm_handle h, void *stream) {
+    if (!h) return PERM_EINVAL;
+    if (cudaStreamSynchronize(h->stream) != cudaSuccess) return PERM_EDEVICE;
+    if (h->own_stream) cudaStreamDestroy(h->stream);
+    h->stream = (cudaStream_t)stream;
+    h->own_stream = false;
+    return PERM_OK;
+}
+
+static RunDev make_params(perm_handle h) {
+    RunDev P;
+    std::memset(&P, 0, sizeof(P));
+    P.d = h->cfg.d; P.n_max = h->cfg.n_max; P.n_seq = h->cfg.n_seq; P.alg = h->cfg.alg;
+    P.log2h = h->log2h; P.S = h->lanes; P.stride = h->stride;
+    P.worker_warps = h->worker_warps; P.slots = h->slots;
+    P.stack_cache = h->stack_cache;
+    P.key0 = (uint32_t)h->cfg.seed ^ h->cfg.run_id;
+    P.key1 = (uint32_t)(h->cfg.seed >> 32);
+    P.tour_limit = h->tour_limit;
+    P.seq_target = h->seq_target;
+    P.refresh_ns = h->cfg.refresh_ns;
+    P.max_ns = (long long)(h->cfg.max_seconds * 1e9);
+    P.Wn = h->Wn; P.Sn = h->Sn; P.Qn = h->Qn; P.tickets = h->tickets; P.seq_M = h->seq_M;
+    P.X = h->X; P.gstk_meta = h->gstk_meta; P.gstk_w = h->gstk_w;
+    P.steps = h->steps; P.max_stack = h->max_stack; P.copies = h->copies; P.refreshes = h->refreshes; P.status = h->status;
+    P.trace = (h->trace_every > 0) ? h->trace : nullptr;
+    P.trace_coords = h->trace_coords; P.trace_count = h->trace_count; P.trace_cap = h->trace_cap;
+    P.trace_every = h->trace_every > 0 ? h->trace_every : 1;
+    P.trace_tour_every = h->trace_tour_every > 0 ? h->trace_tour_every : 1;
+    return P;
+}
+
+int perm_run(perm_handle h, int64_t tours_per_seq) {
+    if (!h || tours_per_seq < 0) return PERM_EINVAL;
+    if (tours_per_seq == 0) return PERM_OK;
+    cudaError_t e;
+    if (h->cfg.alg == PERM_ALG2) {
+        h->tour_limit += tours_per_seq * (long long)h->cfg.n_seq;
+    } else {
+        h->seq_target += tours_per_seq;
+        e = cudaMemsetAsync(h->tickets, 0, sizeof(unsigned long long), h->stream);
+        if (e != cudaSuccess) return to_code(e);
+    }
+    const RunDev P = make_params(h);
+    e = perm::launch_grow(P, h->thresh, h->key64, h->ctas, h->stream);
+    if (e != cudaSuccess) return to_code(e);
+    if (h->cfg.alg == PERM_ALG2) {
+        e = perm::launch_finalize(h->tickets, h->tour_limit, h->stream);
+        if (e != cudaSuccess) return to_code(e);
+    }
+    return PERM_OK;
+}
+
+static int sync_status(perm_handle h) {
+    cudaError_t e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return to_code(e);
+    int st = 0;
+    e = cudaMemcpy(&st, h->status, sizeof(int), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return to_code(e);
+    h->last_status = st;
+    return st;
+}
+
+int perm_run_sync(perm_handle h, int64_t tours_per_seq) {
+    int rc = perm_run(h, tours_per_seq);
+    if (rc != PERM_OK) return rc;
+    return sync_status(h);
+}
+
+int perm_tables(perm_handle h, double *W_n, double *S_n, double *Q_n, int64_t *M) {
+    if (!h) return PERM_EINVAL;
+    int st = sync_status(h);
+    if (st < 0 && st != PERM_EOVERFLOW && st != PERM_ETIMEOUT) return st;
+    const size_t L = (size_t)h->cfg.n_max + 1, cnt = L * h->ntab;
+    cudaError_t e = cudaSuccess;
+    if (W_n) e = cudaMemcpy(W_n, h->Wn, cnt * sizeof(double), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess && Q_n) e = cudaMemcpy(Q_n, h->Qn, cnt * sizeof(double), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess && S_n) {
+        std::vector<unsigned long long> s(cnt);
+        e = cudaMemcpy(s.data(), h->Sn, cnt * sizeof(unsigned long long), cudaMemcpyDeviceToHost);
+        for (size_t i = 0; i < cnt; ++i) S_n[i] = (double)s[i];
+    }
+    if (e == cudaSuccess && M) {
+        if (h->cfg.alg == PERM_ALG2) {
+            M[0] = h->tour_limit;
+        } else {
+            std::vector<unsigned long long> m(h->cfg.n_seq);
+            e = cudaMemcpy(m.data(), h->seq_M, m.size() * sizeof(unsigned long long), cudaMemcpyDeviceToHost);
+            for (size_t i = 0; i < m.size(); ++i) M[i] = (int64_t)m[i];
+        }
+    }
+    if (e != cudaSuccess) return to_code(e);
+    return st;
+}
+
+int perm_reset(perm_handle h) {
+    if (!h) return PERM_EINVAL;
+    const size_t L = (size_t)h->cfg.n_max + 1, cnt = L * h->ntab;
+    cudaError_t e = cudaMemsetAsync(h->Wn, 0, cnt * sizeof(double), h->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->Qn, 0, cnt * sizeof(double), h->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->Sn, 0, cnt * sizeof(unsigned long long), h->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->tickets, 0, sizeof(unsigned long long), h->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->seq_M, 0, sizeof(unsigned long long) * h->cfg.n_seq, h->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->steps, 0, sizeof(unsigned long long), h->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->copies, 0, sizeof(unsigned long long), h->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->refreshes, 0, sizeof(unsigned long long), h->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->max_stack, 0, sizeof(unsigned long long), h->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->status, 0, sizeof(int), h->stream);
+    if (e == cudaSuccess && h->last_status != PERM_OK)   // a stopped run may leave tour sums behind
+        e = cudaMemsetAsync(h->X, 0, L * (size_t)h->slots * sizeof(double), h->stream);
+    if (e != cudaSuccess) return to_code(e);
+    h->tour_limit = 0;
+    h->seq_target = 0;
+    h->last_status = PERM_OK;
+    return PERM_OK;
+}
+
+int perm_estimates(perm_handle h, double *log_cn, double *S_n, double *relvar_n) {
+    if (!h) return PERM_EINVAL;
+    const size_t L = (size_t)h->cfg.n_max + 1, cnt = L * h->ntab;
+    std::vector<double> W(cnt), S(cnt), Q(cnt);
+    std::vector<int64_t> M(h->ntab);
+    int rc = perm_tables(h, W.data(), S.data(), Q.data(), M.data());
+    if (rc != PERM_OK) return rc;
+    for (size_t n = 0; n < L; ++n) {
+        double est = 0.0, var = 0.0, s = 0.0;
+        bool ok = true;
+        for (int t = 0; t < h->ntab; ++t) {
+            const double w = W[t * L + n], q = Q[t * L + n];
+            s += S[t * L + n];
+            const int64_t m = M[t];
+            if (m < 2) { ok = false; continue; }
+            const double c = w / (double)m;
+            double v = (q / (double)m - c * c) / (double)(m - 1);
+            if (v < 0.0) v = 0.0;
+            est += c;
+            var += v;
+        }
+        est /= (double)h->ntab;
+        var /= (double)h->ntab * (double)h->ntab;
+        if (log_cn) log_cn[n] = est > 0.0 ? std::log(est) + scale_exp_host(h->cfg.d, (int)n) * std::log(2.0) : -INFINITY;
+        if (S_n) S_n[n] = s;
+        if (relvar_n) relvar_n[n] = (ok && est > 0.0) ? var / (est * est) : INFINITY;
+    }
+    return PERM_OK;
+}
+
+int perm_stats(perm_handle h, perm_stats_t *out) {
+    if (!h || !out) return PERM_EINVAL;
+    int st = sync_status(h);
+    if (st < 0 && st != PERM_EOVERFLOW && st != PERM_ETIMEOUT) return st;
+    unsigned long long steps = 0, ms = 0, cp = 0, rf = 0;
+    if (cudaMemcpy(&steps, h->steps, 8, cudaMemcpyDeviceToHost) != cudaSuccess) return PERM_EDEVICE;
+    if (cudaMemcpy(&cp, h->copies, 8, cudaMemcpyDeviceToHost) != cudaSuccess) return PERM_EDEVICE;
+    if (cudaMemcpy(&rf, h->refreshes, 8, cudaMemcpyDeviceToHost) != cudaSuccess) return PERM_EDEVICE;
+    if (cudaMemcpy(&ms, h->max_stack, 8, cudaMemcpyDeviceToHost) != cudaSuccess) return PERM_EDEVICE;
+    out->steps = (int64_t)steps;
+    out->tours = h->cfg.alg == PERM_ALG2 ? h->tour_limit : h->seq_target * h->cfg.n_seq;
+    out->max_stack = (int64_t)ms;
+    out->copies = (int64_t)cp;
+    out->refreshes = (int64_t)rf;
+    out->slots = h->slots;
+    out->ctas = h->ctas;
+    out->lanes_per_warp = h->lanes;
+    out->warps_per_cta = h->worker_warps;
+    out->hash_slots = 1 << h->log2h;
+    out->status = st;
+    out->device_bytes = h->device_bytes;
+    return PERM_OK;
+}
+
+int perm_trace_enable(perm_handle h, int64_t every, int64_t tour_every, int capacity) {
+    if (!h || every < 0 || tour_every < 0 || capacity < 0) return PERM_EINVAL;
+    if (cudaStreamSynchronize(h->stream) != cudaSuccess) return PERM_EDEVICE;
+    if (h->trace) { cudaFree(h->trace); h->trace = nullptr; }
+    if (h->trace_coords) { cudaFree(h->trace_coords); h->trace_coords = nullptr; }
+    h->trace_every = every;
+    h->trace_tour_every = tour_every > 0 ? tour_every : 1;
+    h->trace_cap = 0;
+    if (every == 0 || capacity == 0) { h->trace_every = 0; return PERM_OK; }
+    const size_t L = (size_t)h->cfg.n_max + 1;
+    if (cudaMalloc((void **)&h->trace, sizeof(perm_trace_record) * (size_t)capacity) != cudaSuccess ||
+        cudaMalloc((void **)&h->trace_coords, sizeof(int32_t) * (size_t)capacity * L * h->cfg.d) != cudaSuccess) {
+        h->trace_every = 0;
+        return PERM_ENOMEM;
+    }
+    h->trace_cap = capacity;
+    if (cudaMemset(h->trace_count, 0, 8) != cudaSuccess) return PERM_EDEVICE;
+    return PERM_OK;
+}
+
+int perm_trace_read(perm_handle h, int64_t *count, perm_trace_record *recs, int32_t *coords) {
+    if (!h) return PERM_EINVAL;
+    if (cudaStreamSynchronize(h->stream) != cudaSuccess) return PERM_EDEVICE;
+    unsigned long long c = 0;
+    if (cudaMemcpy(&c, h->trace_count, 8, cudaMemcpyDeviceToHost) != cudaSuccess) return PERM_EDEVICE;
+    if (count) *count = (int64_t)c;
+    const size_t kept = c < (unsigned long long)h->trace_cap ? (size_t)c : (size_t)h->trace_cap;
+    const size_t L = (size_t)h->cfg.n_max + 1;
+    if (recs && kept && cudaMemcpy(recs, h->trace, kept * sizeof(perm_trace_record), cudaMemcpyDeviceToHost) != cudaSuccess)
+        return PERM_EDEVICE;
+    if (coords && kept && cudaMemcpy(coords, h->trace_coords, kept * L * h->cfg.d * sizeof(int32_t), cudaMemcpyDeviceToHost) != cudaSuccess)
+        return PERM_EDEVICE;
+    return PERM_OK;
+}
+
+void perm_destroy(perm_handle h) {
+    if (!h) return;
+    cudaStreamSynchronize(h->stream);
+    free_all(h);
+    if (h->own_stream) cudaStreamDestroy(h->stream);
+    delete h;
+}
+
+int perm_debug_step(int d, int n_max, int B, const int32_t *coords, const int32_t *len,
+                    const double *W, const double *T, const uint64_t *M,
+                    const uint64_t *ordinal, const uint32_t *seq, const uint32_t *tour,
+                    uint64_t seed, uint32_t run_id, int32_t *out_i, float *out_r,
+                    double *out_w, uint64_t *out_K, void *stream) {
+    if ((d != 2 && d != 3) || n_max < 1 || n_max > 512 || B < 0) return PERM_EINVAL;
+    if (B > 0 && (!coords || !len || !W || !T || !M || !ordinal || !seq || !tour || !out_i ||
+                  !out_r || !out_w || !out_K))
+        return PERM_EINVAL;
+    cudaError_t e = perm::launch_debug_step(d, n_max, B, coords, len, W, T, M, ordinal, seq, tour,
+                                            (uint32_t)seed ^ run_id, (uint32_t)(seed >> 32), out_i,
+                                            out_r, out_w, out_K, (cudaStream_t)stream);
+    return to_code(e);
+}
+
+int perm_debug_philox(int B, const uint32_t *ctr, const uint32_t *key, uint32_t *out) {
+    if (B < 0 || (B > 0 && (!ctr || !key || !out))) return PERM_EINVAL;
+    cudaError_t e = perm::launch_debug_philox(B, ctr, key[0], key[1], out, nullptr);
+    if (e != cudaSuccess) return to_code(e);
+    return to_code(cudaDeviceSynchronize());
+}
+
+}  // extern "C"

@@ -1,0 +1,281 @@
+// perm_device.cuh -- device building blocks of the flatPERM growth step.
+//
+// Paper: Campbell and Janse van Rensburg, "Parallel PERM".
+//   Sec. 1, eqs. (1)-(2): a_+ free neighbours of the end-point; the next step is
+//     uniform among them; W = prod a_+.
+//   Sec. 2, eq. (6) and the two paragraphs after it: r = W/[W_n]^sample with the
+//     own weight included; r >= 1 enriches into c copies (c = floor r with
+//     probability ceil r - r, else ceil r) of weight W/c; r < 1 prunes with
+//     probability 1 - r, a survivor carries W/r.
+//
+// Layout conventions shared by the kernels:
+//   - A walk's occupancy hash and its per-site slot list live in shared memory,
+//     interleaved by lane: element i of lane l is at [i * S + l] (S = lanes per
+//     warp), so that every lane always hits its own bank.
+//   - Keys pack the lattice coordinates of a site; 0 is the empty slot.
+//   - Directions: j = 0..2d-1 -> axis j/2, sign + for even j (+x,-x,+y,-y,+z,-z).
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace perm {
+
+// ---------------------------------------------------------------------------
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): ten rounds of two 32x32
+// multiplies with round keys bumped by the Weyl constants.
+// ---------------------------------------------------------------------------
+struct Philox4 { uint32_t x, y, z, w; };
+
+__device__ __forceinline__ Philox4 philox4x32_10(uint32_t c0, uint32_t c1, uint32_t c2,
+                                                 uint32_t c3, uint32_t k0, uint32_t k1) {
+    const uint32_t kM0 = 0xD2511F53u, kM1 = 0xCD9E8D57u;
+    const uint32_t kW0 = 0x9E3779B9u, kW1 = 0xBB67AE85u;
+#pragma unroll
+    for (int round = 0; round < 10; ++round) {
+        const uint32_t hi0 = __umulhi(kM0, c0), lo0 = kM0 * c0;
+        const uint32_t hi1 = __umulhi(kM1, c2), lo1 = kM1 * c2;
+        const uint32_t n0 = hi1 ^ c1 ^ k0, n2 = hi0 ^ c3 ^ k1;
+        c0 = n0; c1 = lo1; c2 = n2; c3 = lo0;
+        k0 += kW0;
+        k1 += kW1;
+    }
+    return {c0, c1, c2, c3};
+}
+
+// ---------------------------------------------------------------------------
+// Site keys.  Key32<2>: 16-bit fields x+32768 | (y+32768)<<16, |x|,|y| <= 32766.
+// Key32<3>: 10-bit fields (c+512) mod 1024, for walks with n_max <= 512: every
+// stored site has |c| <= 511 (field 1..1023, never 0); a probe at |c| = 512
+// gives field 0 and cannot match a stored site.  Key64<3>: 21-bit fields.
+// ---------------------------------------------------------------------------
+template <int D, typename Key> struct KeyCodec;
+
+template <> struct KeyCodec<2, uint32_t> {
+    __device__ __forceinline__ static uint32_t encode(int x, int y, int) {
+        return (uint32_t)(x + 32768) | ((uint32_t)(y + 32768) << 16);
+    }
+    __device__ __forceinline__ static void decode(uint32_t k, int &x, int &y, int &z) {
+        x = (int)(k & 0xFFFFu) - 32768;
+        y = (int)(k >> 16) - 32768;
+        z = 0;
+    }
+};
+
+template <> struct KeyCodec<3, uint32_t> {
+    __device__ __forceinline__ static uint32_t encode(int x, int y, int z) {
+        return ((uint32_t)(x + 512) & 1023u) | (((uint32_t)(y + 512) & 1023u) << 10) |
+               (((uint32_t)(z + 512) & 1023u) << 20);
+    }
+    __device__ __forceinline__ static void decode(uint32_t k, int &x, int &y, int &z) {
+        x = (int)(k & 1023u) - 512;
+        y = (int)((k >> 10) & 1023u) - 512;
+        z = (int)((k >> 20) & 1023u) - 512;
+    }
+};
+
+template <> struct KeyCodec<3, unsigned long long> {
+    __device__ __forceinline__ static unsigned long long encode(int x, int y, int z) {
+        return (unsigned long long)(uint32_t)(x + (1 << 20)) |
+               ((unsigned long long)(uint32_t)(y + (1 << 20)) << 21) |
+               ((unsigned long long)(uint32_t)(z + (1 << 20)) << 42);
+    }
+    __device__ __forceinline__ static void decode(unsigned long long k, int &x, int &y, int &z) {
+        x = (int)(k & 0x1FFFFFull) - (1 << 20);
+        y = (int)((k >> 21) & 0x1FFFFFull) - (1 << 20);
+        z = (int)((k >> 42) & 0x1FFFFFull) - (1 << 20);
+    }
+};
+
+__device__ __forceinline__ uint32_t hash_home(uint32_t k, int log2h) {
+    return (k * 0x9E3779B1u) >> (32 - log2h);
+}
+__device__ __forceinline__ uint32_t hash_home(unsigned long long k, int log2h) {
+    const uint32_t f = (uint32_t)k ^ (uint32_t)(k >> 29) ^ (uint32_t)(k >> 53);
+    return (f * 0x9E3779B1u) >> (32 - log2h);
+}
+
+// Neighbour j of (x, y, z).
+__device__ __forceinline__ void step_coords(int j, int &x, int &y, int &z) {
+    const int s = (j & 1) ? -1 : 1;
+    if (j < 2) x += s; else if (j < 4) y += s; else z += s;
+}
+
+// Insert a key known to be absent; returns its slot, or -1 if the probe
+// sequence wrapped around (table full: impossible at load factor <= 1/2).
+template <typename Key>
+__device__ __forceinline__ int hash_insert(Key *tab, int S, int lane, int log2h, Key k) {
+    const uint32_t mask = (1u << log2h) - 1u;
+    uint32_t s = hash_home(k, log2h);
+    for (int it = 0; it <= (int)mask; ++it) {
+        Key *p = tab + (size_t)s * S + lane;
+        if (*p == (Key)0) { *p = k; return (int)s; }
+        s = (s + 1) & mask;
+    }
+    return -1;
+}
+
+// ---------------------------------------------------------------------------
+// a_+ (Sec. 1): probe the 2d neighbours of the end-point with linear probing.
+// Returns the free mask; slot[j] is the empty slot that ended the probe of a
+// free direction j (its insertion slot while the table is unchanged).
+// ---------------------------------------------------------------------------
+template <int D, typename Key>
+__device__ __forceinline__ int probe_neighbours(const Key *tab, int S, int lane, int log2h,
+                                                int x, int y, int z, int (&slot)[2 * D],
+                                                bool &overflow) {
+    const uint32_t mask = (1u << log2h) - 1u;
+    Key key[2 * D];
+    uint32_t s[2 * D];
+    int pending = (1 << (2 * D)) - 1, freem = 0;
+#pragma unroll
+    for (int j = 0; j < 2 * D; ++j) {
+        int xx = x, yy = y, zz = z;
+        step_coords(j, xx, yy, zz);
+        key[j] = KeyCodec<D, Key>::encode(xx, yy, zz);
+        s[j] = hash_home(key[j], log2h);
+    }
+    for (int it = 0; it <= (int)mask && pending; ++it) {
+        Key v[2 * D];
+#pragma unroll
+        for (int j = 0; j < 2 * D; ++j)
+            v[j] = (pending >> j & 1) ? tab[(size_t)s[j] * S + lane] : key[j];
+#pragma unroll
+        for (int j = 0; j < 2 * D; ++j) {
+            if (!(pending >> j & 1)) continue;
+            if (v[j] == key[j]) {
+                pending &= ~(1 << j);                  // occupied
+            } else if (v[j] == (Key)0) {
+                pending &= ~(1 << j);                  // free: remember the slot
+                freem |= 1 << j;
+                slot[j] = (int)s[j];
+            } else {
+                s[j] = (s[j] + 1) & mask;
+            }
+        }
+    }
+    overflow = pending != 0;
+    return freem;
+}
+
+// ---------------------------------------------------------------------------
+// The ratio r of Sec. 2 in single precision.  Doubles enter through their
+// mantissa rounded to 24 bits (nearest, ties to even; a carry bumps the
+// exponent) and their exponent.  The running average T (before the node's own
+// weight) is carried packed: low word = FP32 bits of the rounded mantissa in
+// [1, 2) (0 if T is zero or subnormal), high word = the biased exponent.
+// r = 1 / (T/W + 1/M): the own weight enters through 1/M, since
+// [W_n] = T + W/M.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t mant24_bits(unsigned long long b, int &ef) {
+    const unsigned long long frac = b & 0xFFFFFFFFFFFFFull;
+    uint32_t keep = (uint32_t)(frac >> 29);
+    const unsigned long long rem = frac & 0x1FFFFFFFull;
+    if (rem > 0x10000000ull || (rem == 0x10000000ull && (keep & 1u))) keep += 1u;
+    if (keep == (1u << 23)) { keep = 0u; ef += 1; }
+    return (127u << 23) | keep;
+}
+
+__device__ __forceinline__ unsigned long long pack_threshold(double T) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(T);
+    int ef = (int)((b >> 52) & 0x7FFull);
+    if (ef == 0) return 0ull;
+    const uint32_t fm = mant24_bits(b, ef);
+    return (unsigned long long)fm | ((unsigned long long)(uint32_t)ef << 32);
+}
+
+__device__ __forceinline__ double unpack_threshold(unsigned long long p) {
+    const uint32_t fm = (uint32_t)p;
+    if (fm == 0u) return 0.0;
+    const uint32_t ef = (uint32_t)(p >> 32);
+    const unsigned long long b = ((unsigned long long)ef << 52) |
+                                 ((unsigned long long)(fm & 0x7FFFFFu) << 29);
+    return __longlong_as_double((long long)b);
+}
+
+__device__ __forceinline__ float ratio_r(int n, double W, unsigned long long Tp,
+                                         unsigned long long M) {
+    if (n == 0) return 1.0f;
+    float rho;
+    const uint32_t tm = (uint32_t)Tp;
+    const unsigned long long wb = (unsigned long long)__double_as_longlong(W);
+    int ew = (int)((wb >> 52) & 0x7FFull);
+    if (tm == 0u) {
+        rho = 0.0f;
+    } else if (ew == 0) {
+        rho = 1.2676506e30f;                                   // 2^100
+    } else {
+        const float fm_w = __uint_as_float(mant24_bits(wb, ew));
+        const float q = __fdiv_rn(__uint_as_float(tm), fm_w);
+        int e = (int)(uint32_t)(Tp >> 32) - ew;
+        e = e > 100 ? 100 : (e < -100 ? -100 : e);
+        rho = __fmul_rn(q, __uint_as_float((uint32_t)(e + 127) << 23));
+    }
+    const float inv_m = __frcp_rn(__ull2float_rn(M));
+    return __frcp_rn(__fadd_rn(rho, inv_m));
+}
+
+// Stored-weight scale: weight of a length-n walk is kept divided by 2^E(n).
+__device__ __forceinline__ int scale_exp(int d, int n) {
+    return d == 2 ? (11 * n) >> 3 : (9 * n) >> 2;
+}
+
+// ---------------------------------------------------------------------------
+// Decision of one node (Sec. 2).  Inputs: a_+ (>= 1), free list packed 3 bits
+// per entry in direction order, r, Philox words w0 (decision) and w1 (steps).
+// Output: c (0 = pruned), the chosen directions packed 3 bits each (first =
+// the copy grown now), and the weight factor F with child weight = W * F at
+// the stored scale of length n+1.  aoc[dE_index][a*8+c] = (a/c) 2^-dE.
+// ---------------------------------------------------------------------------
+struct NodeDecision {
+    int c;
+    uint32_t dirs;
+    double F;
+    unsigned long long K;
+};
+
+__device__ __forceinline__ NodeDecision decide(int a, uint32_t freelist, float r, uint32_t w0,
+                                               uint32_t w1, const double *aoc_row, int dE) {
+    NodeDecision o;
+    o.K = 0ull;
+    if (r >= 1.0f) {
+        const float fl = floorf(r), ce = ceilf(r);
+        const float p = __fsub_rn(ce, r);
+        const unsigned long long Kp = __float2ull_rz(ceilf(__fmul_rn(p, 4294967296.0f)));
+        const float craw = ((unsigned long long)w0 < Kp) ? fl : ce;
+        o.c = (craw >= (float)a) ? a : (int)craw;
+        o.F = aoc_row[a * 8 + o.c];
+    } else {
+        const unsigned long long K = __float2ull_rz(ceilf(__fmul_rn(r, 4294967296.0f)));
+        o.K = K;
+        if (!((unsigned long long)w0 < K)) {
+            o.c = 0;
+            o.F = 0.0;
+            o.dirs = 0u;
+            return o;
+        }
+        o.c = 1;
+        // F = a 2^(32-dE) / K: 1/K from the FP32 reciprocal and one Newton step
+        const double kd = (double)K;
+        const double y0 = (double)__frcp_rn((float)K);
+        const double e = __fma_rn(-kd, y0, 1.0);
+        const double y1 = __fma_rn(y0, e, y0);
+        const double num = __longlong_as_double((long long)((unsigned long long)(1023 + 32 - dE) << 52)) * (double)a;
+        o.F = __dmul_rn(num, y1);
+    }
+    // partial Fisher-Yates: c distinct free steps, draws by multiply-high on w1
+    uint32_t x = w1, list = freelist;
+    for (int i = 0; i < o.c; ++i) {
+        const uint32_t m = (uint32_t)(a - i);
+        const unsigned long long prod = (unsigned long long)x * m;
+        const int j = i + (int)(prod >> 32);
+        x = (uint32_t)prod;
+        const uint32_t vi = (list >> (3 * i)) & 7u, vj = (list >> (3 * j)) & 7u;
+        const uint32_t t = vi ^ vj;
+        list ^= (t << (3 * i)) | (t << (3 * j));
+    }
+    o.dirs = list;
+    return o;
+}
+
+}  // namespace perm

@@ -1,0 +1,669 @@
+// perm_kernels.cu -- persistent flatPERM growth kernel (Algorithms 1 and 2 of
+// Campbell and Janse van Rensburg, "Parallel PERM", Sec. 3) for sm_103a.
+//
+// One thread grows one walk ("slot"); a warp holds up to 32 walks.  Per walk,
+// shared memory holds the occupancy hash (linear probing, deleted in LIFO
+// order on backtrack), the hash slot of every site, and the top of the stack
+// of waiting copies (the rest spills to global memory).  Each thread runs the
+// tours handed to it one after another; a tour is a depth-first traversal of
+// the tree of copies made by enrichment (Sec. 2).
+//
+// Threshold sources for Algorithm 2 (one shared table W, Fig. 1):
+//  - snapshot: every CTA accumulates W_n, S_n and Q_n into shared-memory
+//    deltas; one extra warp per CTA flushes them to the global table every
+//    refresh period and reloads a shared-memory copy of [W_n] = W_n/M.  The
+//    nodes read that copy (a stale but fixed threshold keeps the estimator
+//    unbiased: enrichment and pruning conserve the expected weight for any r).
+//  - fresh: every node adds its weight to the global table with an atomic that
+//    returns the previous sum, and uses it at once (sequential flatPERM exactly
+//    when one walk runs).
+// Algorithm 1 (private tables) always uses the fresh form on its own rows.
+#include <cstdio>
+
+#include "perm_device.cuh"
+#include "perm_kernels.cuh"
+
+namespace perm {
+
+namespace {
+
+constexpr int kStride = 32;        // interleave stride of the snapshot-state kernel
+constexpr int kUnwind = 8;         // hash deletions per walk per iteration
+constexpr int kPoolExtra = 4;      // extra tour tickets fetched per warp (snapshot)
+constexpr unsigned kFull = 0xFFFFFFFFu;
+
+enum LaneState { kNeed = 0, kNode = 1, kUnwindState = 2, kFlush = 3, kDone = 4 };
+enum Outcome { kLeafNmax = 0, kTrapped = 1, kPruned = 2, kChildren = 3 };
+
+struct CtaHead {
+    unsigned long long Ms;   // tours started, as of the last snapshot
+    int done_warps;
+    int pad[13];
+};
+static_assert(sizeof(CtaHead) == 64, "header size");
+
+__device__ __forceinline__ long long global_ns() {
+    long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ void set_status(int *status, int code) {
+    atomicCAS(status, 0, code);
+}
+
+__device__ __forceinline__ size_t align16(size_t b) { return (b + 15) & ~(size_t)15; }
+
+__host__ __device__ __forceinline__ size_t warp_region_bytes(int n_max, int log2h, int K,
+                                                             size_t key_bytes, int stride) {
+    const size_t hash_b = ((((size_t)1 << log2h) * stride * key_bytes) + 15) & ~(size_t)15;
+    const size_t sites_b = (((size_t)n_max * stride * 2) + 15) & ~(size_t)15;
+    const size_t stk_b = (((size_t)K * stride * 4) + 15 & ~(size_t)15) + (size_t)K * stride * 8;
+    return hash_b + sites_b + stk_b;
+}
+
+__host__ __device__ __forceinline__ size_t head_region_bytes(int n_max, bool snapshot) {
+    const size_t L = (size_t)n_max + 1;
+    size_t b = 64 + 2 * 64 * 8;   // header + two a/c tables
+    if (snapshot) b += 8 * L + 8 * L + 8 * L + (((4 * L) + 15) & ~(size_t)15);
+    return (b + 15) & ~(size_t)15;
+}
+
+// a/c * 2^-dE for a, c in 1..7 and the two scale steps dE of the lattice.
+__device__ void fill_aoc(double *aoc, int d, int tid, int nthreads) {
+    const int dE_lo = (d == 2) ? 1 : 2;
+    for (int i = tid; i < 128; i += nthreads) {
+        const int t = i >> 6, a = (i >> 3) & 7, c = i & 7;
+        double v = 0.0;
+        if (a >= 1 && c >= 1) {
+            const double q = __ddiv_rn((double)a, (double)c);
+            const double s = __longlong_as_double((long long)((unsigned long long)(1023 - dE_lo - t) << 52));
+            v = __dmul_rn(q, s);
+        }
+        aoc[i] = v;
+    }
+}
+
+struct NodeOut {
+    int outcome, a, mask;
+    float r;
+    NodeDecision dec;
+    double child_w;
+    bool overflow;
+};
+
+// One node's growth step (Sec. 1 and Sec. 2): a_+, r, decision, steps, child
+// weight.  Shared by the persistent kernel and the snapshot-state kernel.
+template <int D, typename Key>
+__device__ __forceinline__ NodeOut grow_node(const Key *hash, int stride, int lane, int log2h, int n,
+                                             int n_max, int cx, int cy, int cz, double W,
+                                             unsigned long long Tp, unsigned long long M,
+                                             unsigned long long ordinal, uint32_t seq,
+                                             uint32_t tour, uint32_t k0, uint32_t k1,
+                                             const double *aoc, int (&eslot)[2 * D]) {
+    NodeOut o;
+    o.a = 0; o.mask = 0; o.r = 0.0f; o.child_w = 0.0; o.overflow = false;
+    o.dec.c = 0; o.dec.dirs = 0u; o.dec.F = 0.0; o.dec.K = 0ull;
+    const Philox4 w = philox4x32_10((uint32_t)ordinal, (uint32_t)(ordinal >> 32), tour, seq, k0, k1);
+    if (n == n_max) { o.outcome = kLeafNmax; return o; }
+    bool ovf = false;
+    const int fm = probe_neighbours<D, Key>(hash, stride, lane, log2h, cx, cy, cz, eslot, ovf);
+    o.overflow = ovf;
+    o.mask = fm;
+    const int a = __popc(fm);
+    o.a = a;
+    if (a == 0) { o.outcome = kTrapped; return o; }
+    uint32_t freelist = 0u;
+    int cnt = 0;
+#pragma unroll
+    for (int j = 0; j < 2 * D; ++j) {
+        if (fm >> j & 1) { freelist |= (uint32_t)j << (3 * cnt); ++cnt; }
+    }
+    const float r = ratio_r(n, W, Tp, M);
+    o.r = r;
+    const int dE = scale_exp(D, n + 1) - scale_exp(D, n);
+    const int dE_lo = (D == 2) ? 1 : 2;
+    o.dec = decide(a, freelist, r, w.x, w.y, aoc + 64 * (dE - dE_lo), dE);
+    if (o.dec.c == 0) { o.outcome = kPruned; return o; }
+    o.child_w = __dmul_rn(W, o.dec.F);
+    o.outcome = kChildren;
+    return o;
+}
+
+template <int D>
+__device__ __forceinline__ int select_slot(const int (&eslot)[2 * D], int dir) {
+    int s = eslot[0];
+#pragma unroll
+    for (int j = 1; j < 2 * D; ++j) if (j == dir) s = eslot[j];
+    return s;
+}
+
+// ---------------------------------------------------------------------------
+// The persistent growth kernel.
+// ---------------------------------------------------------------------------
+template <int D, typename Key, int MODE>
+__global__ void __launch_bounds__(32 * 9, 1) grow_kernel(const RunDev P) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int L = P.n_max + 1;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const bool snapshot = (MODE == kSnapshot);
+    const int K = P.stack_cache;
+
+    CtaHead *head = reinterpret_cast<CtaHead *>(smem);
+    double *aoc = reinterpret_cast<double *>(smem + 64);
+    unsigned char *p = smem + 64 + 1024;
+    unsigned long long *Tpack = nullptr;
+    double *Wd = nullptr, *Qd = nullptr;
+    unsigned int *Sd = nullptr;
+    if (snapshot) {
+        Tpack = reinterpret_cast<unsigned long long *>(p); p += 8 * (size_t)L;
+        Wd = reinterpret_cast<double *>(p); p += 8 * (size_t)L;
+        Qd = reinterpret_cast<double *>(p); p += 8 * (size_t)L;
+        Sd = reinterpret_cast<unsigned int *>(p); p += align16(4 * (size_t)L);
+    }
+    const int ST = P.stride;
+    const size_t wbytes = warp_region_bytes(P.n_max, P.log2h, K, sizeof(Key), ST);
+    const size_t total = head_region_bytes(P.n_max, snapshot) + wbytes * P.worker_warps;
+
+    // zero everything (empty hashes, zero deltas), then the constant tables
+    for (size_t i = threadIdx.x; i < total / 16; i += blockDim.x)
+        reinterpret_cast<uint4 *>(smem)[i] = make_uint4(0u, 0u, 0u, 0u);
+    __syncthreads();
+    fill_aoc(aoc, D, threadIdx.x, blockDim.x);
+    const long long limit = P.tour_limit;
+    if (snapshot) {
+        unsigned long long Ms = *(volatile unsigned long long *)P.tickets;
+        if ((long long)Ms > limit) Ms = (unsigned long long)limit;
+        const double invM = __ddiv_rn(1.0, (double)(Ms > 0ull ? Ms : 1ull));
+        for (int k = threadIdx.x; k < L; k += blockDim.x)
+            Tpack[k] = pack_threshold(__dmul_rn(*(volatile double *)(P.Wn + k), invM));
+        if (threadIdx.x == 0) head->Ms = Ms;
+    }
+    __syncthreads();
+
+    // ----------------------------------------------------------------------
+    // refresher warp (snapshot form): flush the CTA's deltas, reload [W_n]
+    // ----------------------------------------------------------------------
+    if (snapshot && warp == P.worker_warps) {
+        const long long t0 = global_ns();
+        for (long long it = 0;; ++it) {
+            const int done = __shfl_sync(kFull, *(volatile int *)&head->done_warps, 0);
+            __threadfence_block();
+            for (int k = lane; k < L; k += 32) {
+                const double wv = __longlong_as_double((long long)atomicExch(reinterpret_cast<unsigned long long *>(&Wd[k]), 0ull));
+                if (wv != 0.0) atomicAdd(&P.Wn[k], wv);
+                const unsigned int sv = atomicExch(&Sd[k], 0u);
+                if (sv) atomicAdd(&P.Sn[k], (unsigned long long)sv);
+                const double qv = __longlong_as_double((long long)atomicExch(reinterpret_cast<unsigned long long *>(&Qd[k]), 0ull));
+                if (qv != 0.0) atomicAdd(&P.Qn[k], qv);
+            }
+            if (done >= P.worker_warps) {
+                if (lane == 0) atomicAdd(P.refreshes, (unsigned long long)it);
+                break;
+            }
+            unsigned long long Ms = *(volatile unsigned long long *)P.tickets;
+            if ((long long)Ms > limit) Ms = (unsigned long long)limit;
+            const double invM = __ddiv_rn(1.0, (double)(Ms > 0ull ? Ms : 1ull));
+            for (int k = lane; k < L; k += 32) {
+                const double Wg = *(volatile double *)(P.Wn + k);
+                *(volatile unsigned long long *)&Tpack[k] = pack_threshold(__dmul_rn(Wg, invM));
+            }
+            if (lane == 0) *(volatile unsigned long long *)&head->Ms = Ms;
+            __syncwarp();
+            __nanosleep((unsigned)P.refresh_ns);
+            const bool late = (it & 15) == 0 && global_ns() - t0 > P.max_ns;
+            if (__any_sync(kFull, late)) {
+                if (lane == 0) set_status(P.status, PERM_ETIMEOUT);
+                break;
+            }
+        }
+        return;
+    }
+
+    // ----------------------------------------------------------------------
+    // worker warps
+    // ----------------------------------------------------------------------
+    unsigned char *wb = smem + head_region_bytes(P.n_max, snapshot) + wbytes * warp;
+    Key *hash = reinterpret_cast<Key *>(wb);
+    uint16_t *sites = reinterpret_cast<uint16_t *>(
+        wb + (((((size_t)1 << P.log2h) * ST * sizeof(Key)) + 15) & ~(size_t)15));
+    uint32_t *smeta = reinterpret_cast<uint32_t *>(reinterpret_cast<unsigned char *>(sites) +
+                                                   ((((size_t)P.n_max * ST * 2) + 15) & ~(size_t)15));
+    double *sw = reinterpret_cast<double *>(reinterpret_cast<unsigned char *>(smeta) +
+                                            ((((size_t)K * ST * 4) + 15) & ~(size_t)15));
+
+    const int gwarp = blockIdx.x * P.worker_warps + warp;
+    const int slot = gwarp * P.S + lane;
+    const bool active = lane < P.S && slot < P.slots;
+    const int sidx = active ? slot : 0;
+    double *Xrow = P.X + (size_t)sidx * L;
+    uint32_t *gmeta = P.gstk_meta + (size_t)sidx * P.n_max;
+    double *gwt = P.gstk_w + (size_t)sidx * P.n_max;
+    const unsigned lt_mask = (1u << lane) - 1u;
+    const int dE_lo = (D == 2) ? 1 : 2;
+    (void)dE_lo;
+
+    int state = active ? kNeed : kDone;
+    int n = 0, cx = 0, cy = 0, cz = 0, maxn = 0;
+    double W = 1.0;
+    unsigned long long ordinal = 0ull, g = 0ull;
+    uint32_t seq = 0u, tour = 0u;
+    int top = 0, sbase = 0;
+    int un_lo = 0, un_hi = -1, pend_dir = 0, pend_depth = 0;
+    bool tour_end = false;
+    double pend_w = 0.0;
+    unsigned long long my_steps = 0ull, my_copies = 0ull;
+    int my_max_stack = 0;
+    int cur_seq = -1;
+    long long seq_t = 0;
+    unsigned long long pool_lo = 0ull, pool_hi = 0ull;
+    double *Wrow = P.Wn;
+    unsigned long long *Srow = P.Sn;
+    double *Qrow = P.Qn;
+
+    const long long t_start = global_ns();
+    for (long long iter = 0;; ++iter) {
+        const bool late = (iter & 255) == 0 && global_ns() - t_start > P.max_ns;
+        if (__any_sync(kFull, late)) {
+            if (lane == 0) set_status(P.status, PERM_ETIMEOUT);
+            break;
+        }
+        // ---------------- tour tickets ----------------
+        const unsigned need = __ballot_sync(kFull, state == kNeed);
+        if (need) {
+            if (P.alg == PERM_ALG2) {
+                const unsigned cnt = __popc(need);
+                const unsigned rank = __popc(need & lt_mask);
+                const unsigned long long avail = pool_hi - pool_lo;
+                unsigned long long base = 0ull, take = 0ull;
+                if (avail < cnt) {
+                    take = cnt - avail + (snapshot ? (unsigned long long)kPoolExtra : 0ull);
+                    const int leader = __ffs(need) - 1;
+                    if (lane == leader) base = atomicAdd(P.tickets, take);
+                    base = __shfl_sync(kFull, base, leader);
+                }
+                if (state == kNeed) g = (rank < avail) ? pool_lo + rank : base + (rank - avail);
+                if (avail >= cnt) {
+                    pool_lo += cnt;
+                } else {
+                    pool_lo = base + (cnt - avail);
+                    pool_hi = base + take;
+                }
+                if (state == kNeed) {
+                    if ((long long)g >= limit) {
+                        state = kDone;
+                    } else {
+                        seq = (uint32_t)(g % (unsigned long long)P.n_seq);
+                        tour = (uint32_t)(g / (unsigned long long)P.n_seq);
+                    }
+                }
+            } else if (state == kNeed) {
+                // Algorithm 1: a walk owns a sequence until its tours are done
+                if (cur_seq < 0 || seq_t >= P.seq_target) {
+                    const unsigned long long s = atomicAdd(P.tickets, 1ull);
+                    if (s >= (unsigned long long)P.n_seq) {
+                        state = kDone;
+                    } else {
+                        cur_seq = (int)s;
+                        seq_t = (long long)P.seq_M[s];
+                        Wrow = P.Wn + (size_t)s * L;
+                        Srow = P.Sn + (size_t)s * L;
+                        Qrow = P.Qn + (size_t)s * L;
+                    }
+                }
+                if (state == kNeed && cur_seq >= 0 && seq_t < P.seq_target) {
+                    seq = (uint32_t)cur_seq;
+                    tour = (uint32_t)seq_t;
+                    g = (unsigned long long)seq_t;
+                } else if (state == kNeed) {
+                    cur_seq = -1;          // sequence finished: ask again next round
+                }
+            }
+            if (state == kNeed && (P.alg == PERM_ALG2 || cur_seq >= 0)) {
+                // start a tour at the empty walk (Sec. 1: W(empty) = 1)
+                n = 0; cx = cy = cz = 0; maxn = 0; W = 1.0; ordinal = 0ull;
+                top = 0; sbase = 0;
+                const int s0 = hash_insert<Key>(hash, ST, lane, P.log2h,
+                                                KeyCodec<D, Key>::encode(0, 0, 0));
+                if (s0 < 0) { set_status(P.status, PERM_EOVERFLOW); state = kDone; }
+                else { sites[lane] = (uint16_t)s0; state = kNode; }
+            }
+        }
+        const unsigned live = __ballot_sync(kFull, state != kDone);
+        if (!live) break;
+
+        // ---------------- one node ----------------
+        if (state == kNode) {
+            unsigned long long Tp, Mb;
+            if (snapshot) {
+                atomicAdd(&Wd[n], W);
+                atomicAdd(&Sd[n], 1u);
+                Tp = *(volatile unsigned long long *)&Tpack[n];
+                const unsigned long long Ms = *(volatile unsigned long long *)&head->Ms;
+                Mb = Ms > g + 1ull ? Ms : g + 1ull;
+            } else {
+                const double old = atomicAdd(&Wrow[n], W);
+                atomicAdd(&Srow[n], 1ull);
+                if (P.alg == PERM_ALG2) {
+                    unsigned long long Mt = *(volatile unsigned long long *)P.tickets;
+                    if ((long long)Mt > limit) Mt = (unsigned long long)limit;
+                    Mb = Mt > g + 1ull ? Mt : g + 1ull;
+                } else {
+                    Mb = (unsigned long long)seq_t + 1ull;
+                }
+                Tp = pack_threshold(__ddiv_rn(old, (double)Mb));
+            }
+            atomicAdd(&Xrow[n], W);
+            maxn = n > maxn ? n : maxn;
+            ++my_steps;
+
+            int eslot[2 * D];
+#pragma unroll
+            for (int j = 0; j < 2 * D; ++j) eslot[j] = 0;
+            const NodeOut o = grow_node<D, Key>(hash, ST, lane, P.log2h, n, P.n_max, cx, cy, cz, W, Tp,
+                                                Mb, ordinal, seq, tour, P.key0, P.key1, aoc, eslot);
+            if (o.overflow) set_status(P.status, PERM_EOVERFLOW);
+
+            if (P.trace != nullptr && (ordinal % (unsigned long long)P.trace_every) == 0ull &&
+                ((unsigned long long)tour % (unsigned long long)P.trace_tour_every) == 0ull) {
+                const unsigned long long idx = atomicAdd(P.trace_count, 1ull);
+                if (idx < (unsigned long long)P.trace_cap) {
+                    perm_trace_record *rec = P.trace + idx;
+                    rec->n = n; rec->a_plus = o.a; rec->free_mask = o.mask; rec->c = o.dec.c;
+                    rec->outcome = o.outcome; rec->pad = 0;
+                    for (int i = 0; i < 6; ++i)
+                        rec->dirs[i] = (i < o.dec.c) ? (int)((o.dec.dirs >> (3 * i)) & 7u) : -1;
+                    rec->r = o.r; rec->seq = seq; rec->tour = tour; rec->pad2 = 0u;
+                    rec->ordinal = ordinal; rec->M = Mb; rec->survive_K = o.dec.K;
+                    rec->W = W; rec->T = unpack_threshold(Tp); rec->child_w = o.child_w;
+                    int32_t *cc = P.trace_coords + (size_t)idx * L * D;
+                    for (int k = 0; k < n; ++k) {
+                        int x, y, z;
+                        KeyCodec<D, Key>::decode(hash[(size_t)sites[(size_t)k * ST + lane] * ST + lane], x, y, z);
+                        cc[k * D] = x; cc[k * D + 1] = y;
+                        if (D == 3) cc[k * D + 2] = z;
+                    }
+                    cc[n * D] = cx; cc[n * D + 1] = cy;
+                    if (D == 3) cc[n * D + 2] = cz;
+                }
+            }
+
+            ordinal += 1ull;
+            if (o.outcome == kChildren) {
+                const int c = o.dec.c;
+                my_copies += (unsigned long long)(c - 1);
+                if (c > 1) {
+                    // copies 1..c-1 wait in one record (depth, count, steps, weight)
+                    if (top - sbase == K) {
+                        for (int i = 0; i < K / 2; ++i) {
+                            const int idx = sbase + i;
+                            gmeta[idx] = smeta[(size_t)(idx & (K - 1)) * ST + lane];
+                            gwt[idx] = sw[(size_t)(idx & (K - 1)) * ST + lane];
+                        }
+                        sbase += K / 2;
+                    }
+                    if (top >= P.n_max) {
+                        set_status(P.status, PERM_EOVERFLOW);
+                    } else {
+                        const uint32_t rest = (o.dec.dirs >> 3) & ((1u << (3 * (c - 1))) - 1u);
+                        const int ti = top & (K - 1);
+                        smeta[(size_t)ti * ST + lane] = (uint32_t)n | ((uint32_t)(c - 1) << 16) | (rest << 19);
+                        sw[(size_t)ti * ST + lane] = o.child_w;
+                        ++top;
+                        my_max_stack = top > my_max_stack ? top : my_max_stack;
+                    }
+                }
+                const int dir0 = (int)(o.dec.dirs & 7u);
+                const int s0 = select_slot<D>(eslot, dir0);
+                step_coords(dir0, cx, cy, cz);
+                n += 1;
+                if (n < P.n_max) {
+                    hash[(size_t)s0 * ST + lane] = KeyCodec<D, Key>::encode(cx, cy, cz);
+                    sites[(size_t)n * ST + lane] = (uint16_t)s0;
+                }
+                W = o.child_w;
+            } else {
+                // leaf: resume the most recent waiting copy, or end the tour
+                if (top == sbase && sbase > 0) {
+                    sbase -= K / 2;
+                    for (int i = 0; i < K / 2; ++i) {
+                        const int idx = sbase + i;
+                        smeta[(size_t)(idx & (K - 1)) * ST + lane] = gmeta[idx];
+                        sw[(size_t)(idx & (K - 1)) * ST + lane] = gwt[idx];
+                    }
+                }
+                const int hi = n < P.n_max - 1 ? n : P.n_max - 1;
+                if (top == 0) {
+                    un_lo = 0; un_hi = hi; tour_end = true;
+                } else {
+                    const int ti = (top - 1) & (K - 1);
+                    const uint32_t meta = smeta[(size_t)ti * ST + lane];
+                    const int dp = (int)(meta & 0xFFFFu);
+                    const int cnt = (int)((meta >> 16) & 7u);
+                    const uint32_t dirs = meta >> 19;
+                    pend_dir = (int)(dirs & 7u);
+                    pend_w = sw[(size_t)ti * ST + lane];
+                    pend_depth = dp;
+                    if (cnt <= 1) --top;
+                    else smeta[(size_t)ti * ST + lane] = (uint32_t)dp | ((uint32_t)(cnt - 1) << 16) | ((dirs >> 3) << 19);
+                    un_lo = dp + 1; un_hi = hi; tour_end = false;
+                }
+                state = kUnwindState;
+            }
+        }
+
+        // ---------------- backtrack: LIFO deletions, then resume ----------------
+        if (state == kUnwindState) {
+#pragma unroll
+            for (int i = 0; i < kUnwind; ++i) {
+                const int k = un_hi - i;
+                if (k >= un_lo) hash[(size_t)sites[(size_t)k * ST + lane] * ST + lane] = (Key)0;
+            }
+            un_hi -= kUnwind;
+            if (un_hi < un_lo) {
+                if (tour_end) {
+                    state = kFlush;
+                } else {
+                    const int dp = pend_depth;
+                    KeyCodec<D, Key>::decode(hash[(size_t)sites[(size_t)dp * ST + lane] * ST + lane], cx, cy, cz);
+                    step_coords(pend_dir, cx, cy, cz);
+                    n = dp + 1;
+                    if (n < P.n_max) {
+                        const int s = hash_insert<Key>(hash, ST, lane, P.log2h, KeyCodec<D, Key>::encode(cx, cy, cz));
+                        if (s < 0) { set_status(P.status, PERM_EOVERFLOW); state = kDone; }
+                        else sites[(size_t)n * ST + lane] = (uint16_t)s;
+                    }
+                    W = pend_w;
+                    if (state != kDone) state = kNode;
+                }
+            }
+        }
+
+        // ---------------- end of tour: per-tour sums into Q (whole warp) ----------------
+        unsigned fm = __ballot_sync(kFull, state == kFlush);
+        if (fm) {
+            __threadfence();
+            __syncwarp();
+            while (fm) {
+                const int src = __ffs(fm) - 1;
+                fm &= fm - 1u;
+                const int s_slot = __shfl_sync(kFull, sidx, src);
+                const int s_maxn = __shfl_sync(kFull, maxn, src);
+                const int s_seq = __shfl_sync(kFull, cur_seq, src);
+                double *Xr = P.X + (size_t)s_slot * L;
+                double *Qr = (P.alg == PERM_ALG1) ? P.Qn + (size_t)(s_seq < 0 ? 0 : s_seq) * L : P.Qn;
+                for (int k = lane; k <= s_maxn; k += 32) {
+                    const double x = __ldcg(Xr + k);
+                    if (x != 0.0) {
+                        const double x2 = __dmul_rn(x, x);
+                        if (snapshot) atomicAdd(&Qd[k], x2);
+                        else atomicAdd(&Qr[k], x2);
+                        __stcg(Xr + k, 0.0);
+                    }
+                }
+            }
+            __threadfence();
+            __syncwarp();
+            if (state == kFlush) {
+                if (P.alg == PERM_ALG1) {
+                    seq_t += 1;
+                    P.seq_M[cur_seq] = (unsigned long long)seq_t;
+                }
+                (void)Qrow;
+                state = kNeed;
+            }
+        }
+    }
+
+    // statistics, then tell the refresher this warp is done
+    unsigned long long tot = my_steps, cps = my_copies;
+    int ms = my_max_stack;
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        tot += __shfl_xor_sync(kFull, tot, off);
+        cps += __shfl_xor_sync(kFull, cps, off);
+        const int o = __shfl_xor_sync(kFull, ms, off);
+        ms = o > ms ? o : ms;
+    }
+    if (lane == 0) {
+        atomicAdd(P.steps, tot);
+        atomicAdd(P.copies, cps);
+        atomicMax(P.max_stack, (unsigned long long)ms);
+        __threadfence_block();
+        atomicAdd(&head->done_warps, 1);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Growth step on caller-given snapshot states (one thread per state).
+// ---------------------------------------------------------------------------
+template <int D, typename Key>
+__global__ void __launch_bounds__(32) debug_step_kernel(int n_max, int log2h, int B,
+        const int32_t *coords, const int32_t *len, const double *Wv, const double *Tv,
+        const uint64_t *Mv, const uint64_t *ordv, const uint32_t *seqv, const uint32_t *tourv,
+        uint32_t k0, uint32_t k1, int32_t *out_i, float *out_r, double *out_w, uint64_t *out_K) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int H = 1 << log2h;
+    Key *hash = reinterpret_cast<Key *>(smem);
+    double *aoc = reinterpret_cast<double *>(smem + (size_t)H * kStride * sizeof(Key));
+    const int lane = threadIdx.x;
+    fill_aoc(aoc, D, lane, 32);
+    for (int s = 0; s < H; ++s) hash[(size_t)s * kStride + lane] = (Key)0;
+    __syncwarp();
+    const int b = blockIdx.x * 32 + lane;
+    if (b >= B) return;
+    int32_t *oi = out_i + (size_t)b * 10;
+    const int n = len[b];
+    if (n < 0 || n > n_max) { oi[0] = -1; return; }
+    const int32_t *cb = coords + (size_t)b * (n_max + 1) * D;
+    bool ovf = false;
+    const int top = n < n_max - 1 ? n : n_max - 1;
+    for (int k = 0; k <= top; ++k) {
+        const Key key = KeyCodec<D, Key>::encode(cb[k * D], cb[k * D + 1], D == 3 ? cb[k * D + 2] : 0);
+        if (hash_insert<Key>(hash, kStride, lane, log2h, key) < 0) ovf = true;
+    }
+    const int cx = cb[n * D], cy = cb[n * D + 1], cz = (D == 3) ? cb[n * D + 2] : 0;
+    int eslot[2 * D];
+    const NodeOut o = grow_node<D, Key>(hash, kStride, lane, log2h, n, n_max, cx, cy, cz, Wv[b],
+                                        pack_threshold(Tv[b]), Mv[b], ordv[b], seqv[b], tourv[b],
+                                        k0, k1, aoc, eslot);
+    oi[0] = (ovf || o.overflow) ? -2 : o.outcome;
+    oi[1] = o.a;
+    oi[2] = o.mask;
+    oi[3] = o.dec.c;
+    for (int i = 0; i < 6; ++i) oi[4 + i] = (i < o.dec.c) ? (int)((o.dec.dirs >> (3 * i)) & 7u) : -1;
+    out_r[b] = o.r;
+    out_w[b] = o.child_w;
+    out_K[b] = o.dec.K;
+}
+
+__global__ void philox_kernel(int B, const uint32_t *ctr, uint32_t k0, uint32_t k1, uint32_t *out) {
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= B) return;
+    const Philox4 w = philox4x32_10(ctr[4 * b], ctr[4 * b + 1], ctr[4 * b + 2], ctr[4 * b + 3], k0, k1);
+    out[4 * b] = w.x; out[4 * b + 1] = w.y; out[4 * b + 2] = w.z; out[4 * b + 3] = w.w;
+}
+
+__global__ void finalize_kernel(unsigned long long *tickets, long long limit) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        if ((long long)*tickets > limit) *tickets = (unsigned long long)limit;
+    }
+}
+
+}  // namespace
+
+size_t cta_smem_bytes(int d, bool key64, int n_max, int log2h, int stack_cache, int worker_warps,
+                      bool snapshot, int stride) {
+    (void)d;
+    return head_region_bytes(n_max, snapshot) +
+           warp_region_bytes(n_max, log2h, stack_cache, key64 ? 8 : 4, stride) * (size_t)worker_warps;
+}
+
+namespace {
+template <int D, typename Key, int MODE>
+cudaError_t launch_one(const RunDev &P, int ctas, cudaStream_t stream) {
+    const bool snapshot = (MODE == kSnapshot);
+    const size_t smem = cta_smem_bytes(D, sizeof(Key) == 8, P.n_max, P.log2h, P.stack_cache,
+                                       P.worker_warps, snapshot, P.stride);
+    cudaError_t e = cudaFuncSetAttribute(grow_kernel<D, Key, MODE>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    const int threads = 32 * (P.worker_warps + (snapshot ? 1 : 0));
+    grow_kernel<D, Key, MODE><<<ctas, threads, smem, stream>>>(P);
+    return cudaGetLastError();
+}
+}  // namespace
+
+cudaError_t launch_grow(const RunDev &P, int thresh_mode, bool key64, int ctas, cudaStream_t stream) {
+    if (P.d == 2) {
+        return thresh_mode == kSnapshot ? launch_one<2, uint32_t, kSnapshot>(P, ctas, stream)
+                                        : launch_one<2, uint32_t, kFresh>(P, ctas, stream);
+    }
+    if (key64) {
+        return thresh_mode == kSnapshot ? launch_one<3, unsigned long long, kSnapshot>(P, ctas, stream)
+                                        : launch_one<3, unsigned long long, kFresh>(P, ctas, stream);
+    }
+    return thresh_mode == kSnapshot ? launch_one<3, uint32_t, kSnapshot>(P, ctas, stream)
+                                    : launch_one<3, uint32_t, kFresh>(P, ctas, stream);
+}
+
+cudaError_t launch_finalize(unsigned long long *tickets, long long limit, cudaStream_t stream) {
+    finalize_kernel<<<1, 32, 0, stream>>>(tickets, limit);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_debug_step(int d, int n_max, int B, const int32_t *coords, const int32_t *len,
+                              const double *W, const double *T, const uint64_t *M,
+                              const uint64_t *ordinal, const uint32_t *seq, const uint32_t *tour,
+                              uint32_t key0, uint32_t key1, int32_t *out_i, float *out_r,
+                              double *out_w, uint64_t *out_K, cudaStream_t stream) {
+    int log2h = 4;
+    while ((1 << log2h) < 2 * n_max) ++log2h;
+    const int blocks = (B + 31) / 32;
+    if (blocks == 0) return cudaSuccess;
+    const size_t key_b = 4;
+    const size_t smem = ((size_t)1 << log2h) * kStride * key_b + 128 * 8;
+    if (d == 2) {
+        cudaError_t e = cudaFuncSetAttribute(debug_step_kernel<2, uint32_t>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        debug_step_kernel<2, uint32_t><<<blocks, 32, smem, stream>>>(n_max, log2h, B, coords, len, W, T,
+                M, ordinal, seq, tour, key0, key1, out_i, out_r, out_w, out_K);
+    } else {
+        cudaError_t e = cudaFuncSetAttribute(debug_step_kernel<3, uint32_t>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        debug_step_kernel<3, uint32_t><<<blocks, 32, smem, stream>>>(n_max, log2h, B, coords, len, W, T,
+                M, ordinal, seq, tour, key0, key1, out_i, out_r, out_w, out_K);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_debug_philox(int B, const uint32_t *ctr, uint32_t k0, uint32_t k1, uint32_t *out,
+                                cudaStream_t stream) {
+    if (B <= 0) return cudaSuccess;
+    philox_kernel<<<(B + 127) / 128, 128, 0, stream>>>(B, ctr, k0, k1, out);
+    return cudaGetLastError();
+}
+
+}  // namespace perm

@@ -1,0 +1,68 @@
+// perm_kernels.cuh -- parameters shared by the kernels and the C-ABI host code.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "perm.h"
+
+namespace perm {
+
+enum ThreshMode { kSnapshot = 0, kFresh = 1 };
+
+// Everything one persistent launch needs (passed by value).
+struct RunDev {
+    int d, n_max, n_seq, alg;
+    int log2h;           // per-walk hash size 2^log2h
+    int S;               // lanes per warp that hold walks
+    int stride;          // interleave stride of per-walk shared arrays (power of 2, >= S)
+    int worker_warps;    // per CTA
+    int slots;           // walks on the device
+    int stack_cache;     // stack records cached per walk in shared memory (power of 2)
+    uint32_t key0, key1; // Philox key
+    long long tour_limit;      // Alg. 2: tickets below this are tours of this launch or earlier
+    long long seq_target;      // Alg. 1: tours per sequence after this launch
+    int refresh_ns;
+    long long max_ns;          // wall-clock bound of the launch (bounded waits)
+    // global tables: Alg. 2 one row, Alg. 1 n_seq rows of n_max+1
+    double *Wn;
+    unsigned long long *Sn;
+    double *Qn;
+    unsigned long long *tickets;   // Alg. 2: tours started (M); Alg. 1: next sequence
+    unsigned long long *seq_M;     // Alg. 1: tours done per sequence
+    // per-walk scratch
+    double *X;                     // slots x (n_max+1): this tour's weight per length
+    uint32_t *gstk_meta;           // slots x n_max
+    double *gstk_w;                // slots x n_max
+    // statistics and status
+    unsigned long long *steps;
+    unsigned long long *max_stack;
+    unsigned long long *copies;
+    unsigned long long *refreshes;
+    int *status;
+    // optional sampled trace
+    perm_trace_record *trace;
+    int32_t *trace_coords;
+    unsigned long long *trace_count;
+    int trace_cap;
+    long long trace_every, trace_tour_every;
+};
+
+// Shared-memory bytes of one CTA.
+size_t cta_smem_bytes(int d, bool key64, int n_max, int log2h, int stack_cache, int worker_warps,
+                      bool snapshot, int stride);
+
+cudaError_t launch_grow(const RunDev &P, int thresh_mode, bool key64, int ctas,
+                        cudaStream_t stream);
+cudaError_t launch_finalize(unsigned long long *tickets, long long limit, cudaStream_t stream);
+cudaError_t set_smem_limits();
+
+cudaError_t launch_debug_step(int d, int n_max, int B, const int32_t *coords, const int32_t *len,
+                              const double *W, const double *T, const uint64_t *M,
+                              const uint64_t *ordinal, const uint32_t *seq, const uint32_t *tour,
+                              uint32_t key0, uint32_t key1, int32_t *out_i, float *out_r,
+                              double *out_w, uint64_t *out_K, cudaStream_t stream);
+cudaError_t launch_debug_philox(int B, const uint32_t *ctr, uint32_t k0, uint32_t k1, uint32_t *out,
+                                cudaStream_t stream);
+
+}  // namespace perm

@@ -1,0 +1,66 @@
+"""Helpers for the GPU tests: device buffers via torch, calls through the C ABI."""
+import numpy as np
+
+from paper_2002_03000_gb300 import _native as nat
+
+
+def torch_cuda():
+    import torch
+    if not torch.cuda.is_available():
+        import pytest
+        pytest.skip("no CUDA device")
+    return torch
+
+
+def debug_step(states, d, n_max, seed, run_id=0):
+    """Run the growth step of the CUDA path on snapshot states (list of dicts
+    from tests.inputs) through perm_debug_step; returns host numpy arrays."""
+    torch = torch_cuda()
+    B = len(states)
+    L = n_max + 1
+    coords = np.zeros((B, L, d), dtype=np.int32)
+    length = np.zeros(B, dtype=np.int32)
+    for b, st in enumerate(states):
+        w = st["walk"]
+        coords[b, : w.shape[0]] = w
+        length[b] = w.shape[0] - 1
+    dev = "cuda"
+    t = lambda a, dt: torch.as_tensor(np.ascontiguousarray(a)).to(dtype=dt, device=dev)
+    c_t = t(coords.reshape(-1), torch.int32)
+    l_t = t(length, torch.int32)
+    W_t = t(np.array([s["W"] for s in states], dtype=np.float64), torch.float64)
+    T_t = t(np.array([s["T"] for s in states], dtype=np.float64), torch.float64)
+    u64 = lambda key: np.array([s[key] for s in states], dtype=np.uint64).view(np.int64)
+    u32 = lambda key: np.array([s[key] for s in states], dtype=np.uint32).view(np.int32)
+    M_t = t(u64("M"), torch.int64)
+    o_t = t(u64("ordinal"), torch.int64)
+    s_t = t(u32("seq"), torch.int32)
+    u_t = t(u32("tour"), torch.int32)
+    out_i = torch.zeros(B * 10, dtype=torch.int32, device=dev)
+    out_r = torch.zeros(B, dtype=torch.float32, device=dev)
+    out_w = torch.zeros(B, dtype=torch.float64, device=dev)
+    out_K = torch.zeros(B, dtype=torch.int64, device=dev)
+    stream = torch.cuda.current_stream().cuda_stream
+    nat.perm_debug_step(d, n_max, B, c_t.data_ptr(), l_t.data_ptr(), W_t.data_ptr(), T_t.data_ptr(),
+                        M_t.data_ptr(), o_t.data_ptr(), s_t.data_ptr(), u_t.data_ptr(), seed, run_id,
+                        out_i.data_ptr(), out_r.data_ptr(), out_w.data_ptr(), out_K.data_ptr(), stream)
+    torch.cuda.synchronize()
+    return (out_i.cpu().numpy().reshape(B, 10), out_r.cpu().numpy(), out_w.cpu().numpy(),
+            out_K.cpu().numpy().astype(np.uint64))
+
+
+def debug_philox(ctrs, key):
+    torch = torch_cuda()
+    ctr = np.ascontiguousarray(ctrs, dtype=np.uint32).reshape(-1)
+    B = ctr.size // 4
+    c_t = torch.as_tensor(ctr.view(np.int32)).cuda()
+    out = torch.zeros(B * 4, dtype=torch.int32, device="cuda")
+    nat.perm_debug_philox(B, c_t.data_ptr(), key, out.data_ptr())
+    return out.cpu().numpy().view(np.uint32).reshape(B, 4)
+
+
+def Run(*args, **kw):
+    """pg.Run with a short per-launch time bound for tests."""
+    import paper_2002_03000_gb300 as pg
+    kw.setdefault("max_seconds", 120.0)
+    return pg.Run(*args, **kw)
