@@ -66,6 +66,9 @@ typedef struct {
     int refresh_ns;    /* snapshot refresh period in ns; 0 = default (4000) */
     double max_seconds;/* wall-clock bound of one launch; past it the kernel stops and the
                           run reports PERM_ETIMEOUT; 0 = default (600) */
+    int ramp_c0;       /* Algorithm 2 admission: at most ramp_c0 + ramp_gamma * (finished
+                          tours) tours are in flight.  0 = default (32); < 0 = no limit */
+    double ramp_gamma; /* see ramp_c0; 0 = default (1.0) */
 } perm_config;
 
 /* Fill cfg with defaults for (d, n_max, n_seq, seed). */
@@ -116,6 +119,7 @@ typedef struct {
     int64_t max_stack;    /* deepest per-walk stack of waiting copies seen */
     int64_t copies;       /* extra copies pushed by enrichment (c - 1 per node), cumulative */
     int64_t refreshes;    /* threshold refreshes summed over CTAs, cumulative */
+    int64_t iterations;   /* main-loop iterations summed over worker warps, cumulative */
     int slots, ctas, lanes_per_warp, warps_per_cta;
     int hash_slots;       /* per-walk occupancy hash size */
     int status;           /* PERM_OK or the device-side error of the last run */

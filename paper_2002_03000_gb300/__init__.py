@@ -14,7 +14,7 @@ class Run:
 
     def __init__(self, d, n_max, n_seq, seed, run_id=0, alg=PERM_ALG2,
                  threshold=PERM_THRESH_SNAPSHOT, slots=0, lanes_per_warp=0, refresh_ns=0,
-                 max_seconds=0.0):
+                 max_seconds=0.0, ramp_c0=0, ramp_gamma=0.0):
         cfg = _native.perm_config_init(d, n_max, n_seq, seed)
         cfg.run_id = run_id
         cfg.alg = alg
@@ -23,6 +23,8 @@ class Run:
         cfg.lanes_per_warp = lanes_per_warp
         cfg.refresh_ns = refresh_ns
         cfg.max_seconds = max_seconds
+        cfg.ramp_c0 = ramp_c0
+        cfg.ramp_gamma = ramp_gamma
         self.d, self.n_max, self.n_seq, self.alg = d, n_max, n_seq, alg
         self.h = _native.perm_create_ex(cfg)
 

@@ -38,12 +38,12 @@ class perm_config(C.Structure):
     _fields_ = [("d", C.c_int), ("n_max", C.c_int), ("n_seq", C.c_int), ("seed", C.c_uint64),
                 ("run_id", C.c_uint32), ("alg", C.c_int), ("threshold", C.c_int),
                 ("slots", C.c_int), ("lanes_per_warp", C.c_int), ("refresh_ns", C.c_int),
-                ("max_seconds", C.c_double)]
+                ("max_seconds", C.c_double), ("ramp_c0", C.c_int), ("ramp_gamma", C.c_double)]
 
 
 class perm_stats_t(C.Structure):
     _fields_ = [("steps", C.c_int64), ("tours", C.c_int64), ("max_stack", C.c_int64),
-                ("copies", C.c_int64), ("refreshes", C.c_int64),
+                ("copies", C.c_int64), ("refreshes", C.c_int64), ("iterations", C.c_int64),
                 ("slots", C.c_int), ("ctas", C.c_int), ("lanes_per_warp", C.c_int),
                 ("warps_per_cta", C.c_int), ("hash_slots", C.c_int), ("status", C.c_int),
                 ("device_bytes", C.c_int64)]

@@ -31,6 +31,7 @@ struct perm_run_s {
     double *Wn = nullptr, *Qn = nullptr, *X = nullptr, *gstk_w = nullptr;
     unsigned long long *Sn = nullptr, *tickets = nullptr, *seq_M = nullptr;
     unsigned long long *steps = nullptr, *max_stack = nullptr, *copies = nullptr, *refreshes = nullptr, *trace_count = nullptr;
+    unsigned long long *iterations = nullptr, *finished = nullptr;
     uint32_t *gstk_meta = nullptr;
     int *status = nullptr;
     perm_trace_record *trace = nullptr;
@@ -65,7 +66,7 @@ int dalloc(perm_handle h, T **p, size_t count) {
 
 void free_all(perm_handle h) {
     void *ptrs[] = {h->Wn, h->Qn, h->X, h->gstk_w, h->Sn, h->tickets, h->seq_M, h->steps,
-                    h->max_stack, h->copies, h->refreshes, h->trace_count, h->gstk_meta, h->status, h->trace,
+                    h->max_stack, h->copies, h->refreshes, h->iterations, h->finished, h->trace_count, h->gstk_meta, h->status, h->trace,
                     h->trace_coords};
     for (void *p : ptrs) if (p) cudaFree(p);
 }
@@ -95,6 +96,8 @@ void perm_config_init(perm_config *cfg, int d, int n_max, int n_seq, uint64_t se
     cfg->lanes_per_warp = 0;
     cfg->refresh_ns = 0;
     cfg->max_seconds = 0.0;
+    cfg->ramp_c0 = 0;
+    cfg->ramp_gamma = 0.0;
 }
 
 const char *perm_strerror(int code) {
@@ -118,6 +121,7 @@ int perm_create_ex(perm_handle *out, const perm_config *cfg) {
     if (cfg->alg != PERM_ALG1 && cfg->alg != PERM_ALG2) return PERM_EINVAL;
     if (cfg->threshold != PERM_THRESH_SNAPSHOT && cfg->threshold != PERM_THRESH_FRESH) return PERM_EINVAL;
     if (cfg->slots < 0 || cfg->refresh_ns < 0 || !(cfg->max_seconds >= 0.0)) return PERM_EINVAL;
+    if (!(cfg->ramp_gamma >= 0.0) || cfg->ramp_gamma > 1e6) return PERM_EINVAL;
     const int lpw = cfg->lanes_per_warp;
     if (lpw != 0 && (lpw < 1 || lpw > 32)) return PERM_EINVAL;
     const bool key64 = (d == 3 && n_max > 512);
@@ -134,6 +138,8 @@ int perm_create_ex(perm_handle *out, const perm_config *cfg) {
     if (h->cfg.refresh_ns == 0) h->cfg.refresh_ns = 4000;
     if (h->cfg.refresh_ns > 1000000) h->cfg.refresh_ns = 1000000;
     if (h->cfg.max_seconds == 0.0) h->cfg.max_seconds = 600.0;
+    if (h->cfg.ramp_c0 == 0) h->cfg.ramp_c0 = 32;
+    if (h->cfg.ramp_gamma == 0.0) h->cfg.ramp_gamma = 1.0;
     h->device = dev;
     h->num_sms = prop.multiProcessorCount;
     h->key64 = key64;
@@ -197,6 +203,8 @@ int perm_create_ex(perm_handle *out, const perm_config *cfg) {
     if (rc == PERM_OK) rc = dalloc(h, &h->max_stack, 1);
     if (rc == PERM_OK) rc = dalloc(h, &h->copies, 1);
     if (rc == PERM_OK) rc = dalloc(h, &h->refreshes, 1);
+    if (rc == PERM_OK) rc = dalloc(h, &h->iterations, 1);
+    if (rc == PERM_OK) rc = dalloc(h, &h->finished, 1);
     if (rc == PERM_OK) rc = dalloc(h, &h->trace_count, 1);
     if (rc == PERM_OK) rc = dalloc(h, &h->status, 1);
     if (rc == PERM_OK) rc = to_code(cudaStreamSynchronize(h->stream));
@@ -240,7 +248,11 @@ static RunDev make_params(perm_handle h) {
     P.max_ns = (long long)(h->cfg.max_seconds * 1e9);
     P.Wn = h->Wn; P.Sn = h->Sn; P.Qn = h->Qn; P.tickets = h->tickets; P.seq_M = h->seq_M;
     P.X = h->X; P.gstk_meta = h->gstk_meta; P.gstk_w = h->gstk_w;
-    P.steps = h->steps; P.max_stack = h->max_stack; P.copies = h->copies; P.refreshes = h->refreshes; P.status = h->status;
+    P.steps = h->steps; P.max_stack = h->max_stack; P.copies = h->copies; P.refreshes = h->refreshes; P.iterations = h->iterations;
+    P.finished = h->finished;
+    P.ramp_c0 = h->cfg.ramp_c0 < 0 ? -1 : (long long)h->cfg.ramp_c0;
+    P.ramp_gamma_q16 = (unsigned long long)(h->cfg.ramp_gamma * 65536.0);
+    P.status = h->status;
     P.trace = (h->trace_every > 0) ? h->trace : nullptr;
     P.trace_coords = h->trace_coords; P.trace_count = h->trace_count; P.trace_cap = h->trace_cap;
     P.trace_every = h->trace_every > 0 ? h->trace_every : 1;
@@ -322,6 +334,8 @@ int perm_reset(perm_handle h) {
     if (e == cudaSuccess) e = cudaMemsetAsync(h->steps, 0, sizeof(unsigned long long), h->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(h->copies, 0, sizeof(unsigned long long), h->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(h->refreshes, 0, sizeof(unsigned long long), h->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->iterations, 0, sizeof(unsigned long long), h->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->finished, 0, sizeof(unsigned long long), h->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(h->max_stack, 0, sizeof(unsigned long long), h->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(h->status, 0, sizeof(int), h->stream);
     if (e == cudaSuccess && h->last_status != PERM_OK)   // a stopped run may leave tour sums behind
@@ -367,16 +381,18 @@ int perm_stats(perm_handle h, perm_stats_t *out) {
     if (!h || !out) return PERM_EINVAL;
     int st = sync_status(h);
     if (st < 0 && st != PERM_EOVERFLOW && st != PERM_ETIMEOUT) return st;
-    unsigned long long steps = 0, ms = 0, cp = 0, rf = 0;
+    unsigned long long steps = 0, ms = 0, cp = 0, rf = 0, it = 0;
     if (cudaMemcpy(&steps, h->steps, 8, cudaMemcpyDeviceToHost) != cudaSuccess) return PERM_EDEVICE;
     if (cudaMemcpy(&cp, h->copies, 8, cudaMemcpyDeviceToHost) != cudaSuccess) return PERM_EDEVICE;
     if (cudaMemcpy(&rf, h->refreshes, 8, cudaMemcpyDeviceToHost) != cudaSuccess) return PERM_EDEVICE;
+    if (cudaMemcpy(&it, h->iterations, 8, cudaMemcpyDeviceToHost) != cudaSuccess) return PERM_EDEVICE;
     if (cudaMemcpy(&ms, h->max_stack, 8, cudaMemcpyDeviceToHost) != cudaSuccess) return PERM_EDEVICE;
     out->steps = (int64_t)steps;
     out->tours = h->cfg.alg == PERM_ALG2 ? h->tour_limit : h->seq_target * h->cfg.n_seq;
     out->max_stack = (int64_t)ms;
     out->copies = (int64_t)cp;
     out->refreshes = (int64_t)rf;
+    out->iterations = (int64_t)it;
     out->slots = h->slots;
     out->ctas = h->ctas;
     out->lanes_per_warp = h->lanes;

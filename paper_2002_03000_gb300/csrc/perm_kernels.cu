@@ -65,7 +65,7 @@ __host__ __device__ __forceinline__ size_t warp_region_bytes(int n_max, int log2
 __host__ __device__ __forceinline__ size_t head_region_bytes(int n_max, bool snapshot) {
     const size_t L = (size_t)n_max + 1;
     size_t b = 64 + 2 * 64 * 8;   // header + two a/c tables
-    if (snapshot) b += 8 * L + 8 * L + 8 * L + (((4 * L) + 15) & ~(size_t)15);
+    if (snapshot) b += 8 * L + 8 * L + (((4 * L) + 15) & ~(size_t)15);
     return (b + 15) & ~(size_t)15;
 }
 
@@ -153,12 +153,11 @@ __global__ void __launch_bounds__(32 * 9, 1) grow_kernel(const RunDev P) {
     double *aoc = reinterpret_cast<double *>(smem + 64);
     unsigned char *p = smem + 64 + 1024;
     unsigned long long *Tpack = nullptr;
-    double *Wd = nullptr, *Qd = nullptr;
+    double *Wd = nullptr;
     unsigned int *Sd = nullptr;
     if (snapshot) {
         Tpack = reinterpret_cast<unsigned long long *>(p); p += 8 * (size_t)L;
         Wd = reinterpret_cast<double *>(p); p += 8 * (size_t)L;
-        Qd = reinterpret_cast<double *>(p); p += 8 * (size_t)L;
         Sd = reinterpret_cast<unsigned int *>(p); p += align16(4 * (size_t)L);
     }
     const int ST = P.stride;
@@ -189,13 +188,15 @@ __global__ void __launch_bounds__(32 * 9, 1) grow_kernel(const RunDev P) {
         for (long long it = 0;; ++it) {
             const int done = __shfl_sync(kFull, *(volatile int *)&head->done_warps, 0);
             __threadfence_block();
+            // W_n deltas feed the thresholds and go out every period; the
+            // sample counts S_n are only read after the launch
             for (int k = lane; k < L; k += 32) {
                 const double wv = __longlong_as_double((long long)atomicExch(reinterpret_cast<unsigned long long *>(&Wd[k]), 0ull));
                 if (wv != 0.0) atomicAdd(&P.Wn[k], wv);
-                const unsigned int sv = atomicExch(&Sd[k], 0u);
-                if (sv) atomicAdd(&P.Sn[k], (unsigned long long)sv);
-                const double qv = __longlong_as_double((long long)atomicExch(reinterpret_cast<unsigned long long *>(&Qd[k]), 0ull));
-                if (qv != 0.0) atomicAdd(&P.Qn[k], qv);
+                if (done >= P.worker_warps) {
+                    const unsigned int sv = atomicExch(&Sd[k], 0u);
+                    if (sv) atomicAdd(&P.Sn[k], (unsigned long long)sv);
+                }
             }
             if (done >= P.worker_warps) {
                 if (lane == 0) atomicAdd(P.refreshes, (unsigned long long)it);
@@ -257,9 +258,10 @@ __global__ void __launch_bounds__(32 * 9, 1) grow_kernel(const RunDev P) {
     int cur_seq = -1;
     long long seq_t = 0;
     unsigned long long pool_lo = 0ull, pool_hi = 0ull;
+    bool waiting = false;
+    unsigned long long my_iters = 0ull;
     double *Wrow = P.Wn;
     unsigned long long *Srow = P.Sn;
-    double *Qrow = P.Qn;
 
     const long long t_start = global_ns();
     for (long long iter = 0;; ++iter) {
@@ -277,19 +279,52 @@ __global__ void __launch_bounds__(32 * 9, 1) grow_kernel(const RunDev P) {
                 const unsigned long long avail = pool_hi - pool_lo;
                 unsigned long long base = 0ull, take = 0ull;
                 if (avail < cnt) {
-                    take = cnt - avail + (snapshot ? (unsigned long long)kPoolExtra : 0ull);
+                    // fetch tickets; admission keeps tours in flight at most
+                    // c0 + gamma * finished (a partial grant is allowed)
                     const int leader = __ffs(need) - 1;
-                    if (lane == leader) base = atomicAdd(P.tickets, take);
+                    const unsigned long long want = cnt - avail + (snapshot ? (unsigned long long)kPoolExtra : 0ull);
+                    if (lane == leader) {
+                        if (P.ramp_c0 < 0) {
+                            base = atomicAdd(P.tickets, want);
+                            take = want;
+                        } else {
+                            for (int attempt = 0; attempt < 64; ++attempt) {
+                                const unsigned long long t_now = *(volatile unsigned long long *)P.tickets;
+                                const unsigned long long f_now = *(volatile unsigned long long *)P.finished;
+                                unsigned long long k = want;
+                                if ((long long)t_now < limit) {
+                                    const unsigned long long allow = (unsigned long long)P.ramp_c0 +
+                                                                     ((f_now * P.ramp_gamma_q16) >> 16);
+                                    const unsigned long long infl = t_now - (f_now < t_now ? f_now : t_now);
+                                    k = allow > infl ? allow - infl : 0ull;
+                                    k = k < want ? k : want;
+                                }
+                                if (k == 0ull) break;
+                                if (atomicCAS(P.tickets, t_now, t_now + k) == t_now) {
+                                    base = t_now;
+                                    take = k;
+                                    break;
+                                }
+                            }
+                        }
+                    }
                     base = __shfl_sync(kFull, base, leader);
+                    take = __shfl_sync(kFull, take, leader);
                 }
-                if (state == kNeed) g = (rank < avail) ? pool_lo + rank : base + (rank - avail);
+                const bool served = rank < avail + take;
+                if (state == kNeed && served) g = (rank < avail) ? pool_lo + rank : base + (rank - avail);
                 if (avail >= cnt) {
                     pool_lo += cnt;
-                } else {
+                } else if (avail + take > cnt) {
                     pool_lo = base + (cnt - avail);
                     pool_hi = base + take;
+                } else {
+                    pool_lo = pool_hi = 0ull;      // pool and grant all handed out
                 }
-                if (state == kNeed) {
+                if (state == kNeed && !served) {
+                    waiting = true;                // not admitted yet: try again next round
+                } else if (state == kNeed) {
+                    waiting = false;
                     if ((long long)g >= limit) {
                         state = kDone;
                     } else {
@@ -308,7 +343,6 @@ __global__ void __launch_bounds__(32 * 9, 1) grow_kernel(const RunDev P) {
                         seq_t = (long long)P.seq_M[s];
                         Wrow = P.Wn + (size_t)s * L;
                         Srow = P.Sn + (size_t)s * L;
-                        Qrow = P.Qn + (size_t)s * L;
                     }
                 }
                 if (state == kNeed && cur_seq >= 0 && seq_t < P.seq_target) {
@@ -319,7 +353,7 @@ __global__ void __launch_bounds__(32 * 9, 1) grow_kernel(const RunDev P) {
                     cur_seq = -1;          // sequence finished: ask again next round
                 }
             }
-            if (state == kNeed && (P.alg == PERM_ALG2 || cur_seq >= 0)) {
+            if (state == kNeed && !waiting && (P.alg == PERM_ALG2 || cur_seq >= 0)) {
                 // start a tour at the empty walk (Sec. 1: W(empty) = 1)
                 n = 0; cx = cy = cz = 0; maxn = 0; W = 1.0; ordinal = 0ull;
                 top = 0; sbase = 0;
@@ -331,6 +365,8 @@ __global__ void __launch_bounds__(32 * 9, 1) grow_kernel(const RunDev P) {
         }
         const unsigned live = __ballot_sync(kFull, state != kDone);
         if (!live) break;
+        ++my_iters;
+        if (__all_sync(kFull, state == kDone || (state == kNeed && waiting))) __nanosleep(500);
 
         // ---------------- one node ----------------
         if (state == kNode) {
@@ -492,24 +528,32 @@ __global__ void __launch_bounds__(32 * 9, 1) grow_kernel(const RunDev P) {
                 const int s_seq = __shfl_sync(kFull, cur_seq, src);
                 double *Xr = P.X + (size_t)s_slot * L;
                 double *Qr = (P.alg == PERM_ALG1) ? P.Qn + (size_t)(s_seq < 0 ? 0 : s_seq) * L : P.Qn;
-                for (int k = lane; k <= s_maxn; k += 32) {
-                    const double x = __ldcg(Xr + k);
-                    if (x != 0.0) {
-                        const double x2 = __dmul_rn(x, x);
-                        if (snapshot) atomicAdd(&Qd[k], x2);
-                        else atomicAdd(&Qr[k], x2);
-                        __stcg(Xr + k, 0.0);
+                // eight loads in flight per lane, then the squares go straight to Q_n
+                for (int k0 = 0; k0 <= s_maxn; k0 += 32 * 8) {
+                    double x[8];
+#pragma unroll
+                    for (int u = 0; u < 8; ++u) {
+                        const int k = k0 + u * 32 + lane;
+                        x[u] = (k <= s_maxn) ? __ldcg(Xr + k) : 0.0;
+                    }
+#pragma unroll
+                    for (int u = 0; u < 8; ++u) {
+                        const int k = k0 + u * 32 + lane;
+                        if (x[u] != 0.0) {
+                            atomicAdd(&Qr[k], __dmul_rn(x[u], x[u]));
+                            __stcg(Xr + k, 0.0);
+                        }
                     }
                 }
             }
             __threadfence();
             __syncwarp();
             if (state == kFlush) {
+                if (P.alg == PERM_ALG2) atomicAdd(P.finished, 1ull);
                 if (P.alg == PERM_ALG1) {
                     seq_t += 1;
                     P.seq_M[cur_seq] = (unsigned long long)seq_t;
                 }
-                (void)Qrow;
                 state = kNeed;
             }
         }
@@ -528,6 +572,7 @@ __global__ void __launch_bounds__(32 * 9, 1) grow_kernel(const RunDev P) {
     if (lane == 0) {
         atomicAdd(P.steps, tot);
         atomicAdd(P.copies, cps);
+        atomicAdd(P.iterations, my_iters);
         atomicMax(P.max_stack, (unsigned long long)ms);
         __threadfence_block();
         atomicAdd(&head->done_warps, 1);

@@ -39,6 +39,10 @@ struct RunDev {
     unsigned long long *max_stack;
     unsigned long long *copies;
     unsigned long long *refreshes;
+    unsigned long long *iterations;
+    unsigned long long *finished;  // Alg. 2: tours finished (admission of new tours)
+    long long ramp_c0;             // admission: in flight <= c0 + gamma * finished
+    unsigned long long ramp_gamma_q16;
     int *status;
     // optional sampled trace
     perm_trace_record *trace;
