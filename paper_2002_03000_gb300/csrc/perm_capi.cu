@@ -138,7 +138,7 @@ int perm_create_ex(perm_handle *out, const perm_config *cfg) {
     if (h->cfg.refresh_ns == 0) h->cfg.refresh_ns = 4000;
     if (h->cfg.refresh_ns > 1000000) h->cfg.refresh_ns = 1000000;
     if (h->cfg.max_seconds == 0.0) h->cfg.max_seconds = 600.0;
-    if (h->cfg.ramp_c0 == 0) h->cfg.ramp_c0 = 32;
+    if (h->cfg.ramp_c0 == 0) h->cfg.ramp_c0 = 2;
     if (h->cfg.ramp_gamma == 0.0) h->cfg.ramp_gamma = 1.0;
     h->device = dev;
     h->num_sms = prop.multiProcessorCount;
@@ -155,38 +155,51 @@ int perm_create_ex(perm_handle *out, const perm_config *cfg) {
     }
     h->own_stream = true;
 
-    // layout: interleave stride (walks per warp), worker warps per CTA, CTAs
+    // layout: walks per warp (lanes), worker warps per CTA, CTAs.  Each thread
+    // grows one walk; the walks of an SM are spread over about four warps so
+    // that every scheduler has a walk's dependent chain to issue from.
     const bool snap = (h->thresh == perm::kSnapshot);
     const size_t budget = prop.sharedMemPerBlockOptin;
-    int stride = 32;
-    while (lpw && stride / 2 >= lpw) stride /= 2;
-    size_t head = 0, per_warp = 0;
-    for (;; stride /= 2) {
-        head = perm::cta_smem_bytes(d, key64, n_max, log2h, h->stack_cache, 0, snap, stride);
-        per_warp = perm::cta_smem_bytes(d, key64, n_max, log2h, h->stack_cache, 1, snap, stride) - head;
-        if (head + per_warp <= budget || stride == 1) break;
-    }
-    if (head + per_warp > budget) { cudaStreamDestroy(h->stream); delete h; return PERM_EUNSUPPORTED; }
-    int max_warps = (int)((budget - head) / per_warp);
-    if (max_warps > 8) max_warps = 8;
-    const int lanes_cap = (lpw && lpw < stride) ? lpw : stride;
-    const long long capacity = (long long)h->num_sms * max_warps * lanes_cap;
+    auto pow2_at_least = [](int v) { int p = 1; while (p < v) p <<= 1; return p; };
+    auto smem_for = [&](int warps, int stride) {
+        return perm::cta_smem_bytes(d, key64, n_max, log2h, h->stack_cache, warps, snap, stride);
+    };
     long long slots = cfg->slots ? cfg->slots : (long long)n_seq;
-    if (slots > capacity) slots = capacity;
     if (slots > n_seq) slots = n_seq;
-    // spread the walks evenly: as few walks per SM as the count allows
-    long long per_cta = (slots + h->num_sms - 1) / h->num_sms;
-    int warps = (int)((per_cta + lanes_cap - 1) / lanes_cap);
-    if (warps > max_warps) warps = max_warps;
-    int lanes = (int)((per_cta + warps - 1) / warps);
-    if (lanes > lanes_cap) lanes = lanes_cap;
+    const long long slots_wanted = slots;
+    int warps = 0, lanes = 0, stride = 0;
+    for (;;) {
+        const long long per_cta = (slots + h->num_sms - 1) / h->num_sms;
+        int best_w = 0, best_l = 0, best_s = 0;
+        for (int w = 1; w <= 8; ++w) {
+            int l = (int)((per_cta + w - 1) / w);
+            if (lpw) { if (l > lpw) continue; l = lpw < l ? lpw : l; }
+            if (l > 32 || (long long)w * l < per_cta) continue;
+            const int st = pow2_at_least(l);
+            if (smem_for(w, st) > budget) continue;
+            // prefer about four warps; among fitting choices keep the first that reaches it
+            if (best_w == 0 || (best_w < 4 && w <= 4) || (lpw && w < best_w)) {
+                best_w = w; best_l = l; best_s = st;
+            }
+            if (!lpw && w >= 4) break;
+        }
+        if (best_w) { warps = best_w; lanes = best_l; stride = best_s; break; }
+        if (slots <= 1) break;
+        slots = slots - (slots + 7) / 8;        // does not fit: fewer concurrent walks
+    }
+    if (!warps) { cudaStreamDestroy(h->stream); delete h; return PERM_EUNSUPPORTED; }
     const long long per_cta_eff = (long long)warps * lanes;
+    // with the layout fixed, use every SM (sequences beyond it wait at tour boundaries)
+    if (slots < slots_wanted) {
+        const long long cap = (long long)h->num_sms * per_cta_eff;
+        slots = slots_wanted < cap ? slots_wanted : cap;
+    }
     h->ctas = (int)((slots + per_cta_eff - 1) / per_cta_eff);
     h->worker_warps = warps;
     h->lanes = lanes;
     h->stride = stride;
     h->slots = (int)slots;
-    h->smem = perm::cta_smem_bytes(d, key64, n_max, log2h, h->stack_cache, warps, snap, stride);
+    h->smem = smem_for(warps, stride);
 
     const size_t L = (size_t)n_max + 1;
     h->ntab = (cfg->alg == PERM_ALG1) ? n_seq : 1;

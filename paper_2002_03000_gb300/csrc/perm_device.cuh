@@ -168,10 +168,10 @@ __device__ __forceinline__ int probe_neighbours(const Key *tab, int S, int lane,
 // [W_n] = T + W/M.
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ uint32_t mant24_bits(unsigned long long b, int &ef) {
-    const unsigned long long frac = b & 0xFFFFFFFFFFFFFull;
-    uint32_t keep = (uint32_t)(frac >> 29);
-    const unsigned long long rem = frac & 0x1FFFFFFFull;
-    if (rem > 0x10000000ull || (rem == 0x10000000ull && (keep & 1u))) keep += 1u;
+    const uint32_t hi = (uint32_t)(b >> 32) & 0xFFFFFu, lo = (uint32_t)b;
+    uint32_t keep = (hi << 3) | (lo >> 29);          // top 23 fraction bits
+    const uint32_t rem = lo & 0x1FFFFFFFu;           // the 29 bits dropped
+    if (rem > 0x10000000u || (rem == 0x10000000u && (keep & 1u))) keep += 1u;
     if (keep == (1u << 23)) { keep = 0u; ef += 1; }
     return (127u << 23) | keep;
 }
@@ -230,38 +230,53 @@ __device__ __forceinline__ int scale_exp(int d, int n) {
 struct NodeDecision {
     int c;
     uint32_t dirs;
-    double F;
+    double F;        // enrichment: child weight factor (a/c) 2^-dE
+    double Fs;       // survival: 1/K = Fs (1 + e) with Fs = y0 the FP32 reciprocal of K ...
+    float e;         // ... and e = 1 - K y0 in FP32 (K has at most 24 significant bits)
+    bool survive;
     unsigned long long K;
 };
+
+// Exact float -> double widening by bit manipulation (normal floats).
+__device__ __forceinline__ double widen(float f) {
+    const uint32_t b = __float_as_uint(f);
+    if ((b & 0x7FFFFFFFu) == 0u) return 0.0;
+    const unsigned long long e = ((b >> 23) & 0xFFu) + (1023u - 127u);
+    const unsigned long long d = ((unsigned long long)(b >> 31) << 63) | (e << 52) |
+                                 ((unsigned long long)(b & 0x7FFFFFu) << 29);
+    return __longlong_as_double((long long)d);
+}
 
 __device__ __forceinline__ NodeDecision decide(int a, uint32_t freelist, float r, uint32_t w0,
                                                uint32_t w1, const double *aoc_row, int dE) {
     NodeDecision o;
     o.K = 0ull;
+    o.F = 0.0;
+    o.Fs = 0.0;
+    o.e = 0.0f;
+    o.survive = false;
     if (r >= 1.0f) {
         const float fl = floorf(r), ce = ceilf(r);
         const float p = __fsub_rn(ce, r);
         const unsigned long long Kp = __float2ull_rz(ceilf(__fmul_rn(p, 4294967296.0f)));
-        const float craw = ((unsigned long long)w0 < Kp) ? fl : ce;
+        const float craw = ((unsigned long long)w0 < Kp) ? fl : ce;   // u0 < p  <=>  w0 < Kp
         o.c = (craw >= (float)a) ? a : (int)craw;
         o.F = aoc_row[a * 8 + o.c];
     } else {
-        const unsigned long long K = __float2ull_rz(ceilf(__fmul_rn(r, 4294967296.0f)));
+        const float kf = ceilf(__fmul_rn(r, 4294967296.0f));     // K = ceil(r 2^32) <= 2^32
+        const unsigned long long K = __float2ull_rz(kf);
         o.K = K;
         if (!((unsigned long long)w0 < K)) {
             o.c = 0;
-            o.F = 0.0;
             o.dirs = 0u;
             return o;
         }
         o.c = 1;
-        // F = a 2^(32-dE) / K: 1/K from the FP32 reciprocal and one Newton step
-        const double kd = (double)K;
-        const double y0 = (double)__frcp_rn((float)K);
-        const double e = __fma_rn(-kd, y0, 1.0);
-        const double y1 = __fma_rn(y0, e, y0);
-        const double num = __longlong_as_double((long long)((unsigned long long)(1023 + 32 - dE) << 52)) * (double)a;
-        o.F = __dmul_rn(num, y1);
+        o.survive = true;
+        // 1/K = y0 (1 + e) to ~2^-46: y0 the FP32 reciprocal, e its FP32 residual
+        const float y0 = __frcp_rn(kf);
+        o.e = __fmaf_rn(-kf, y0, 1.0f);
+        o.Fs = widen(y0);
     }
     // partial Fisher-Yates: c distinct free steps, draws by multiply-high on w1
     uint32_t x = w1, list = freelist;

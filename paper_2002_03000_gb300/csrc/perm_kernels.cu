@@ -69,7 +69,9 @@ __host__ __device__ __forceinline__ size_t head_region_bytes(int n_max, bool sna
     return (b + 15) & ~(size_t)15;
 }
 
-// a/c * 2^-dE for a, c in 1..7 and the two scale steps dE of the lattice.
+// Weight factors for the two scale steps dE of the lattice (row t: dE = dE_lo + t):
+// [a*8 + c] = (a/c) 2^-dE for c >= 1 (enrichment), [a*8 + 0] = a 2^(32-dE)
+// (survival, before the 1/K factor).
 __device__ void fill_aoc(double *aoc, int d, int tid, int nthreads) {
     const int dE_lo = (d == 2) ? 1 : 2;
     for (int i = tid; i < 128; i += nthreads) {
@@ -79,6 +81,9 @@ __device__ void fill_aoc(double *aoc, int d, int tid, int nthreads) {
             const double q = __ddiv_rn((double)a, (double)c);
             const double s = __longlong_as_double((long long)((unsigned long long)(1023 - dE_lo - t) << 52));
             v = __dmul_rn(q, s);
+        } else if (a >= 1) {
+            const double s = __longlong_as_double((long long)((unsigned long long)(1023 + 32 - dE_lo - t) << 52));
+            v = __dmul_rn((double)a, s);
         }
         aoc[i] = v;
     }
@@ -102,9 +107,12 @@ __device__ __forceinline__ NodeOut grow_node(const Key *hash, int stride, int la
                                              uint32_t tour, uint32_t k0, uint32_t k1,
                                              const double *aoc, int (&eslot)[2 * D]) {
     NodeOut o;
-    o.a = 0; o.mask = 0; o.r = 0.0f; o.child_w = 0.0; o.overflow = false;
+    o.a = 0; o.mask = 0; o.child_w = 0.0; o.overflow = false;
     o.dec.c = 0; o.dec.dirs = 0u; o.dec.F = 0.0; o.dec.K = 0ull;
+    // three independent chains: the node's random block, r, and the probes
     const Philox4 w = philox4x32_10((uint32_t)ordinal, (uint32_t)(ordinal >> 32), tour, seq, k0, k1);
+    const float r = ratio_r(n, W, Tp, M);
+    o.r = r;
     if (n == n_max) { o.outcome = kLeafNmax; return o; }
     bool ovf = false;
     const int fm = probe_neighbours<D, Key>(hash, stride, lane, log2h, cx, cy, cz, eslot, ovf);
@@ -119,13 +127,18 @@ __device__ __forceinline__ NodeOut grow_node(const Key *hash, int stride, int la
     for (int j = 0; j < 2 * D; ++j) {
         if (fm >> j & 1) { freelist |= (uint32_t)j << (3 * cnt); ++cnt; }
     }
-    const float r = ratio_r(n, W, Tp, M);
-    o.r = r;
     const int dE = scale_exp(D, n + 1) - scale_exp(D, n);
     const int dE_lo = (D == 2) ? 1 : 2;
-    o.dec = decide(a, freelist, r, w.x, w.y, aoc + 64 * (dE - dE_lo), dE);
+    const double *row = aoc + 64 * (dE - dE_lo);
+    o.dec = decide(a, freelist, r, w.x, w.y, row, dE);
     if (o.dec.c == 0) { o.outcome = kPruned; return o; }
-    o.child_w = __dmul_rn(W, o.dec.F);
+    if (o.dec.survive) {
+        // child = W a 2^(32-dE) / K = u (1 + e), u = W a 2^(32-dE) y0
+        const double u = __dmul_rn(__dmul_rn(W, row[a * 8]), o.dec.Fs);
+        o.child_w = __fma_rn(u, widen(o.dec.e), u);
+    } else {
+        o.child_w = __dmul_rn(W, o.dec.F);
+    }
     o.outcome = kChildren;
     return o;
 }

@@ -69,6 +69,14 @@ def test_alg1_matches_oracle(d, n_max, N, tours):
     assert np.allclose(lc_g, lc_o, rtol=0, atol=1e-10)
 
 
+# Relative-error floor for nearly deterministic lengths.  With many concurrent
+# walks and shared snapshot thresholds, the per-tour variance misses the
+# correlation that a common threshold induces between tours; it matters only
+# where the intrinsic variance is tiny (n = 2: estimated 2.9e-6 against a
+# spread of 7.6e-6 over 20 seeds of 4096 x 8 tours; at n >= 3 the two agree).
+SIGMA_FLOOR = 1e-5
+
+
 def _zs(lc, rv, exact):
     """z-scores of the estimates against exact c_n; an estimate that is exact
     with zero estimated variance (short lengths, where every weight is equal)
@@ -78,7 +86,7 @@ def _zs(lc, rv, exact):
     rv = rv[: len(ex)]
     exact_zero = (np.abs(rel) < 1e-12) & (rv == 0.0)
     with np.errstate(divide="ignore", invalid="ignore"):
-        z = rel / np.sqrt(rv)
+        z = rel / np.sqrt(rv + SIGMA_FLOOR ** 2)
     return np.where(exact_zero, 0.0, z)
 
 
@@ -104,7 +112,7 @@ def test_snapshot_counting_theorem(d, n_max, N, tours, exact_counts):
     o.run(min(tours, max(1, 200000 // N)))
     lo, So, rvo = o.estimates()
     diff = lc[2:] - lo[2:]
-    var = rv[2:] + rvo[2:]
+    var = rv[2:] + rvo[2:] + 2 * SIGMA_FLOOR ** 2
     with np.errstate(divide="ignore", invalid="ignore"):
         zz = np.where((np.abs(diff) < 1e-12) & (var == 0.0), 0.0, diff / np.sqrt(var))
     assert np.all(np.abs(zz) < 4.0), zz
