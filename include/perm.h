@@ -41,6 +41,8 @@ extern "C" {
 #define PERM_EDEVICE (-4)    /* CUDA error (launch, copy, no device) */
 #define PERM_ETIMEOUT (-5)   /* a bounded device wait ran out; run invalid */
 #define PERM_EUNSUPPORTED (-6) /* configuration this build does not handle */
+#define PERM_ESCRATCH (-7)   /* perm_run_static: the requested walks need more scratch than
+                                the static buffer (PERM_STATIC_SCRATCH_BYTES) holds */
 
 typedef struct perm_run_s *perm_handle;
 
@@ -166,6 +168,38 @@ int perm_debug_step(int d, int n_max, int B, const int32_t *coords, const int32_
                     const uint64_t *ordinal, const uint32_t *seq, const uint32_t *tour,
                     uint64_t seed, uint32_t run_id, int32_t *out_i, float *out_r,
                     double *out_w, uint64_t *out_K, void *stream);
+
+/* perm_run_static -- one complete Algorithm-2 growth run that allocates
+ * nothing (the paper has no counterpart: this serves callers that cannot
+ * call cudaMalloc -- a process whose device memory is owned by another
+ * allocator, a plugin inside one, or a loop that must not allocate because
+ * cudaMalloc/cudaFree can synchronise the device).
+ *
+ * All scratch (tour counters, status, per-walk tour sums and stack spill
+ * areas) lives in one file-scope device array of PERM_STATIC_SCRATCH_BYTES
+ * that every GPU loading the library holds until exit.  The first call on a
+ * device looks up the array's device address (make that first call before
+ * any stream capture).  Every call shares the array and leaves its contents
+ * behind; each call clears what must start at zero.  Calls whose work
+ * overlaps on the GPU race on the array: do not overlap them.
+ *
+ * cfg: as for perm_create_ex; alg must be PERM_ALG2.  cfg->slots = 0 runs
+ * as many walks at once as the buffer holds (sequences beyond that are
+ * time-sliced at tour boundaries); an explicit cfg->slots whose scratch
+ * exceeds the buffer is rejected with PERM_ESCRATCH.  Starts from empty tables and
+ * grows tours_per_seq tours of each of cfg->n_seq sequences (M = n_seq *
+ * tours_per_seq).
+ * W_n, S_n, Q_n: caller-owned DEVICE arrays of n_max+1 entries, overwritten
+ * with the raw tables at the stored scale (as perm_tables; S_n as uint64).
+ * steps: host pointer (may be NULL) for the number of growth steps.
+ * stream: a cudaStream_t (NULL = legacy default stream); the call waits for it.
+ * Returns PERM_OK, PERM_EINVAL, PERM_EUNSUPPORTED, PERM_ESCRATCH (the requested
+ * walks' scratch exceeds the buffer), PERM_EDEVICE, or a kernel status
+ * (PERM_EOVERFLOW, PERM_ETIMEOUT).  No cudaMalloc, cudaFree or allocating
+ * library routine is called. */
+#define PERM_STATIC_SCRATCH_BYTES (32u << 20)
+int perm_run_static(const perm_config *cfg, int64_t tours_per_seq, double *W_n,
+                    unsigned long long *S_n, double *Q_n, int64_t *steps, void *stream);
 
 /* Philox4x32-10 on the device for B counters (test support).  ctr[B*4],
  * key[2] on the host, out[B*4]; ctr and out are DEVICE pointers.  Waits. */

@@ -21,6 +21,8 @@ PERM_EOVERFLOW = -3
 PERM_EDEVICE = -4
 PERM_ETIMEOUT = -5
 PERM_EUNSUPPORTED = -6
+PERM_ESCRATCH = -7
+PERM_STATIC_SCRATCH_BYTES = 32 << 20
 PERM_ALG1 = 1
 PERM_ALG2 = 2
 PERM_THRESH_SNAPSHOT = 0
@@ -31,6 +33,7 @@ EXPORTS = (
     "perm_config_init", "perm_create", "perm_create_ex", "perm_set_stream", "perm_run", "perm_reset",
     "perm_run_sync", "perm_estimates", "perm_tables", "perm_stats", "perm_trace_enable",
     "perm_trace_read", "perm_destroy", "perm_strerror", "perm_debug_step", "perm_debug_philox",
+    "perm_run_static",
 )
 
 
@@ -99,6 +102,7 @@ def load(path: str = LIB_PATH):
     L.perm_strerror.restype = C.c_char_p
     L.perm_debug_step.argtypes = [C.c_int, C.c_int, C.c_int] + [vp] * 8 + [u64, u32] + [vp] * 4 + [vp]
     L.perm_debug_philox.argtypes = [C.c_int, vp, C.POINTER(u32), vp]
+    L.perm_run_static.argtypes = [C.POINTER(perm_config), i64, vp, vp, vp, C.POINTER(i64), vp]
     for name in EXPORTS:
         if name not in ("perm_config_init", "perm_destroy", "perm_strerror"):
             getattr(L, name).restype = C.c_int
@@ -203,6 +207,16 @@ def perm_debug_step(d, n_max, B, coords, length, W, T, M, ordinal, seq, tour, se
     _check(load().perm_debug_step(d, n_max, B, coords, length, W, T, M, ordinal, seq, tour,
                                   seed, run_id, out_i, out_r, out_w, out_K, stream),
            "perm_debug_step")
+
+
+def perm_run_static(cfg, tours_per_seq, W_dev, S_dev, Q_dev, stream=0):
+    """One growth run with the library's static scratch (no allocation).  W_dev,
+    S_dev, Q_dev are device pointers of n_max+1 float64/uint64/float64 entries.
+    Returns the number of growth steps."""
+    steps = C.c_int64(0)
+    _check(load().perm_run_static(C.byref(cfg), tours_per_seq, W_dev, S_dev, Q_dev,
+                                  C.byref(steps), stream), "perm_run_static")
+    return steps.value
 
 
 def perm_debug_philox(B, ctr_dev, key, out_dev):

@@ -109,6 +109,7 @@ const char *perm_strerror(int code) {
         case PERM_EDEVICE: return "CUDA device error";
         case PERM_ETIMEOUT: return "bounded device wait ran out";
         case PERM_EUNSUPPORTED: return "configuration not supported";
+        case PERM_ESCRATCH: return "requested walks need more scratch than the static buffer holds";
         default: return "unknown error";
     }
 }
