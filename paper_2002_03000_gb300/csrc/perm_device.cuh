@@ -108,7 +108,7 @@ __device__ __forceinline__ int hash_insert(Key *tab, int S, int lane, int log2h,
     const uint32_t mask = (1u << log2h) - 1u;
     uint32_t s = hash_home(k, log2h);
     for (int it = 0; it <= (int)mask; ++it) {
-        Key *p = tab + (size_t)s * S + lane;
+        Key *p = tab + (s * (uint32_t)S + (uint32_t)lane);
         if (*p == (Key)0) { *p = k; return (int)s; }
         s = (s + 1) & mask;
     }
@@ -118,7 +118,9 @@ __device__ __forceinline__ int hash_insert(Key *tab, int S, int lane, int log2h,
 // ---------------------------------------------------------------------------
 // a_+ (Sec. 1): probe the 2d neighbours of the end-point with linear probing.
 // Returns the free mask; slot[j] is the empty slot that ended the probe of a
-// free direction j (its insertion slot while the table is unchanged).
+// free direction j (its insertion slot while the table is unchanged).  Each
+// round loads all 2d slots and updates the probes with selects (no branches);
+// at load factor <= 1/2 almost every probe ends in the first round.
 // ---------------------------------------------------------------------------
 template <int D, typename Key>
 __device__ __forceinline__ int probe_neighbours(const Key *tab, int S, int lane, int log2h,
@@ -127,35 +129,33 @@ __device__ __forceinline__ int probe_neighbours(const Key *tab, int S, int lane,
     const uint32_t mask = (1u << log2h) - 1u;
     Key key[2 * D];
     uint32_t s[2 * D];
-    int pending = (1 << (2 * D)) - 1, freem = 0;
 #pragma unroll
     for (int j = 0; j < 2 * D; ++j) {
         int xx = x, yy = y, zz = z;
         step_coords(j, xx, yy, zz);
         key[j] = KeyCodec<D, Key>::encode(xx, yy, zz);
         s[j] = hash_home(key[j], log2h);
+        slot[j] = 0;
     }
-    for (int it = 0; it <= (int)mask && pending; ++it) {
+    uint32_t pending = (1u << (2 * D)) - 1u, freem = 0u;
+    for (int it = 0; it <= (int)mask; ++it) {
         Key v[2 * D];
 #pragma unroll
-        for (int j = 0; j < 2 * D; ++j)
-            v[j] = (pending >> j & 1) ? tab[(size_t)s[j] * S + lane] : key[j];
+        for (int j = 0; j < 2 * D; ++j) v[j] = tab[s[j] * (uint32_t)S + (uint32_t)lane];
 #pragma unroll
         for (int j = 0; j < 2 * D; ++j) {
-            if (!(pending >> j & 1)) continue;
-            if (v[j] == key[j]) {
-                pending &= ~(1 << j);                  // occupied
-            } else if (v[j] == (Key)0) {
-                pending &= ~(1 << j);                  // free: remember the slot
-                freem |= 1 << j;
-                slot[j] = (int)s[j];
-            } else {
-                s[j] = (s[j] + 1) & mask;
-            }
+            const bool pend = (pending >> j) & 1u;
+            const bool hit = v[j] == key[j];
+            const bool emp = v[j] == (Key)0;          // keys are never 0
+            slot[j] = (pend && emp) ? (int)s[j] : slot[j];
+            freem |= (uint32_t)(pend && emp) << j;
+            pending &= ~((uint32_t)(pend && (hit || emp)) << j);
+            s[j] = (s[j] + 1u) & mask;                // harmless for resolved probes
         }
+        if (pending == 0u) break;
     }
-    overflow = pending != 0;
-    return freem;
+    overflow = pending != 0u;
+    return (int)freem;
 }
 
 // ---------------------------------------------------------------------------
@@ -195,24 +195,22 @@ __device__ __forceinline__ double unpack_threshold(unsigned long long p) {
 
 __device__ __forceinline__ float ratio_r(int n, double W, unsigned long long Tp,
                                          unsigned long long M) {
-    if (n == 0) return 1.0f;
-    float rho;
+    // 1/M in FP32 (M rounded to nearest first; 32-bit conversion when it fits)
+    const float Mf = (M >> 32) ? __ull2float_rn(M) : __uint2float_rn((uint32_t)M);
+    const float inv_m = __frcp_rn(Mf);
     const uint32_t tm = (uint32_t)Tp;
     const unsigned long long wb = (unsigned long long)__double_as_longlong(W);
-    int ew = (int)((wb >> 52) & 0x7FFull);
-    if (tm == 0u) {
-        rho = 0.0f;
-    } else if (ew == 0) {
-        rho = 1.2676506e30f;                                   // 2^100
-    } else {
-        const float fm_w = __uint_as_float(mant24_bits(wb, ew));
-        const float q = __fdiv_rn(__uint_as_float(tm), fm_w);
-        int e = (int)(uint32_t)(Tp >> 32) - ew;
-        e = e > 100 ? 100 : (e < -100 ? -100 : e);
-        rho = __fmul_rn(q, __uint_as_float((uint32_t)(e + 127) << 23));
-    }
-    const float inv_m = __frcp_rn(__ull2float_rn(M));
-    return __frcp_rn(__fadd_rn(rho, inv_m));
+    const int ew0 = (int)((uint32_t)(wb >> 52) & 0x7FFu);
+    int ew = ew0;
+    const float fm_w = __uint_as_float(mant24_bits(wb, ew));
+    const float q = __fdiv_rn(__uint_as_float(tm | (tm == 0u ? (127u << 23) : 0u)), fm_w);
+    int e = (int)(uint32_t)(Tp >> 32) - ew;
+    e = e > 100 ? 100 : (e < -100 ? -100 : e);
+    float rho = __fmul_rn(q, __uint_as_float((uint32_t)(e + 127) << 23));
+    rho = (ew0 == 0) ? 1.2676506e30f : rho;          // W zero or subnormal: 2^100
+    rho = (tm == 0u) ? 0.0f : rho;                  // T zero: 0 (checked first)
+    const float r = __frcp_rn(__fadd_rn(rho, inv_m));
+    return n == 0 ? 1.0f : r;
 }
 
 // Stored-weight scale: weight of a length-n walk is kept divided by 2^E(n).
@@ -247,6 +245,31 @@ __device__ __forceinline__ double widen(float f) {
     return __longlong_as_double((long long)d);
 }
 
+// w < ceil(x) for an integer w in [0, 2^32) and a float x in [0, 2^32], exactly,
+// with integer operations only (u0 < x/2^32  <=>  w < ceil(x)).
+__device__ __forceinline__ bool below_ceil(uint32_t w, float x) {
+    const uint32_t b = __float_as_uint(x);
+    const int e = (int)(b >> 23) - 127;
+    const uint32_t m = (b & 0x7FFFFFu) | 0x800000u;
+    const int sh = 23 - e;
+    const uint32_t c_small = (m + ((1u << (sh & 31)) - 1u)) >> (sh & 31);   // 0 <= e < 23
+    const uint32_t c_big = m << ((e - 23) & 31);                             // 23 <= e < 32
+    const uint32_t c = (e >= 23) ? c_big : c_small;
+    return (b == 0u) ? false : (e >= 32 ? true : (e < 0 ? (w == 0u) : (w < c)));
+}
+
+// ceil(x) for a float x in [0, 2^32] as a 64-bit integer (exact).
+__device__ __forceinline__ unsigned long long ceil_u64(float x) {
+    const uint32_t b = __float_as_uint(x);
+    if (b == 0u) return 0ull;
+    const int e = (int)(b >> 23) - 127;
+    const unsigned long long m = (b & 0x7FFFFFu) | 0x800000u;
+    if (e < 0) return 1ull;
+    if (e >= 23) return m << (e - 23);
+    const int sh = 23 - e;
+    return (m + ((1ull << sh) - 1ull)) >> sh;
+}
+
 __device__ __forceinline__ NodeDecision decide(int a, uint32_t freelist, float r, uint32_t w0,
                                                uint32_t w1, const double *aoc_row, int dE) {
     NodeDecision o;
@@ -255,41 +278,39 @@ __device__ __forceinline__ NodeDecision decide(int a, uint32_t freelist, float r
     o.Fs = 0.0;
     o.e = 0.0f;
     o.survive = false;
-    if (r >= 1.0f) {
-        const float fl = floorf(r), ce = ceilf(r);
-        const float p = __fsub_rn(ce, r);
-        const unsigned long long Kp = __float2ull_rz(ceilf(__fmul_rn(p, 4294967296.0f)));
-        const float craw = ((unsigned long long)w0 < Kp) ? fl : ce;   // u0 < p  <=>  w0 < Kp
-        o.c = (craw >= (float)a) ? a : (int)craw;
-        o.F = aoc_row[a * 8 + o.c];
-    } else {
-        const float kf = ceilf(__fmul_rn(r, 4294967296.0f));     // K = ceil(r 2^32) <= 2^32
-        const unsigned long long K = __float2ull_rz(kf);
-        o.K = K;
-        if (!((unsigned long long)w0 < K)) {
-            o.c = 0;
-            o.dirs = 0u;
-            return o;
-        }
-        o.c = 1;
-        o.survive = true;
-        // 1/K = y0 (1 + e) to ~2^-46: y0 the FP32 reciprocal, e its FP32 residual
-        const float y0 = __frcp_rn(kf);
-        o.e = __fmaf_rn(-kf, y0, 1.0f);
-        o.Fs = widen(y0);
-    }
+    (void)dE;
+    // enrichment: p = ceil(r) - r; c = floor(r) iff u0 < p; at most a_+ copies
+    const float fl = floorf(r), ce = ceilf(r);
+    const float xp = __fmul_rn(__fsub_rn(ce, r), 4294967296.0f);   // p 2^32, exact
+    const float craw = below_ceil(w0, xp) ? fl : ce;
+    const int c_en = (craw >= (float)a) ? a : (int)craw;
+    // pruning: survive iff u0 < r, i.e. w0 < K = ceil(r 2^32)
+    const float kf = ceilf(__fmul_rn(r, 4294967296.0f));           // K, at most 24 bits
+    const bool surv = below_ceil(w0, kf);
+    const bool enrich = r >= 1.0f;
+    o.c = enrich ? c_en : (surv ? 1 : 0);
+    o.survive = !enrich && surv;
+    o.F = aoc_row[a * 8 + (enrich ? c_en : 0)];
+    if (!enrich) o.K = ceil_u64(kf);
+    // 1/K = y0 (1 + e) to ~2^-46: y0 the FP32 reciprocal, e its FP32 residual
+    const float y0 = __frcp_rn(kf);
+    o.e = __fmaf_rn(-kf, y0, 1.0f);
+    o.Fs = widen(y0);
     // partial Fisher-Yates: c distinct free steps, draws by multiply-high on w1
     uint32_t x = w1, list = freelist;
-    for (int i = 0; i < o.c; ++i) {
-        const uint32_t m = (uint32_t)(a - i);
-        const unsigned long long prod = (unsigned long long)x * m;
-        const int j = i + (int)(prod >> 32);
-        x = (uint32_t)prod;
-        const uint32_t vi = (list >> (3 * i)) & 7u, vj = (list >> (3 * j)) & 7u;
-        const uint32_t t = vi ^ vj;
-        list ^= (t << (3 * i)) | (t << (3 * j));
+#pragma unroll
+    for (int i = 0; i < 6; ++i) {
+        if (i < o.c) {
+            const uint32_t m = (uint32_t)(a - i);
+            const unsigned long long prod = (unsigned long long)x * m;
+            const int j = i + (int)(prod >> 32);
+            x = (uint32_t)prod;
+            const uint32_t vi = (list >> (3 * i)) & 7u, vj = (list >> (3 * j)) & 7u;
+            const uint32_t t = vi ^ vj;
+            list ^= (t << (3 * i)) | (t << (3 * j));
+        }
     }
-    o.dirs = list;
+    o.dirs = (o.c == 0) ? 0u : list;
     return o;
 }
 

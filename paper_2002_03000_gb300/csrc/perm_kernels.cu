@@ -428,7 +428,7 @@ __global__ void __launch_bounds__(32 * 9, 1) grow_kernel(const RunDev P) {
                     int32_t *cc = P.trace_coords + (size_t)idx * L * D;
                     for (int k = 0; k < n; ++k) {
                         int x, y, z;
-                        KeyCodec<D, Key>::decode(hash[(size_t)sites[(size_t)k * ST + lane] * ST + lane], x, y, z);
+                        KeyCodec<D, Key>::decode(hash[(uint32_t)sites[(uint32_t)k * ST + lane] * ST + lane], x, y, z);
                         cc[k * D] = x; cc[k * D + 1] = y;
                         if (D == 3) cc[k * D + 2] = z;
                     }
@@ -446,8 +446,8 @@ __global__ void __launch_bounds__(32 * 9, 1) grow_kernel(const RunDev P) {
                     if (top - sbase == K) {
                         for (int i = 0; i < K / 2; ++i) {
                             const int idx = sbase + i;
-                            gmeta[idx] = smeta[(size_t)(idx & (K - 1)) * ST + lane];
-                            gwt[idx] = sw[(size_t)(idx & (K - 1)) * ST + lane];
+                            gmeta[idx] = smeta[(uint32_t)(idx & (K - 1)) * ST + lane];
+                            gwt[idx] = sw[(uint32_t)(idx & (K - 1)) * ST + lane];
                         }
                         sbase += K / 2;
                     }
@@ -456,8 +456,8 @@ __global__ void __launch_bounds__(32 * 9, 1) grow_kernel(const RunDev P) {
                     } else {
                         const uint32_t rest = (o.dec.dirs >> 3) & ((1u << (3 * (c - 1))) - 1u);
                         const int ti = top & (K - 1);
-                        smeta[(size_t)ti * ST + lane] = (uint32_t)n | ((uint32_t)(c - 1) << 16) | (rest << 19);
-                        sw[(size_t)ti * ST + lane] = o.child_w;
+                        smeta[(uint32_t)ti * ST + lane] = (uint32_t)n | ((uint32_t)(c - 1) << 16) | (rest << 19);
+                        sw[(uint32_t)ti * ST + lane] = o.child_w;
                         ++top;
                         my_max_stack = top > my_max_stack ? top : my_max_stack;
                     }
@@ -467,8 +467,8 @@ __global__ void __launch_bounds__(32 * 9, 1) grow_kernel(const RunDev P) {
                 step_coords(dir0, cx, cy, cz);
                 n += 1;
                 if (n < P.n_max) {
-                    hash[(size_t)s0 * ST + lane] = KeyCodec<D, Key>::encode(cx, cy, cz);
-                    sites[(size_t)n * ST + lane] = (uint16_t)s0;
+                    hash[(uint32_t)s0 * ST + lane] = KeyCodec<D, Key>::encode(cx, cy, cz);
+                    sites[(uint32_t)n * ST + lane] = (uint16_t)s0;
                 }
                 W = o.child_w;
             } else {
@@ -477,8 +477,8 @@ __global__ void __launch_bounds__(32 * 9, 1) grow_kernel(const RunDev P) {
                     sbase -= K / 2;
                     for (int i = 0; i < K / 2; ++i) {
                         const int idx = sbase + i;
-                        smeta[(size_t)(idx & (K - 1)) * ST + lane] = gmeta[idx];
-                        sw[(size_t)(idx & (K - 1)) * ST + lane] = gwt[idx];
+                        smeta[(uint32_t)(idx & (K - 1)) * ST + lane] = gmeta[idx];
+                        sw[(uint32_t)(idx & (K - 1)) * ST + lane] = gwt[idx];
                     }
                 }
                 const int hi = n < P.n_max - 1 ? n : P.n_max - 1;
@@ -486,15 +486,15 @@ __global__ void __launch_bounds__(32 * 9, 1) grow_kernel(const RunDev P) {
                     un_lo = 0; un_hi = hi; tour_end = true;
                 } else {
                     const int ti = (top - 1) & (K - 1);
-                    const uint32_t meta = smeta[(size_t)ti * ST + lane];
+                    const uint32_t meta = smeta[(uint32_t)ti * ST + lane];
                     const int dp = (int)(meta & 0xFFFFu);
                     const int cnt = (int)((meta >> 16) & 7u);
                     const uint32_t dirs = meta >> 19;
                     pend_dir = (int)(dirs & 7u);
-                    pend_w = sw[(size_t)ti * ST + lane];
+                    pend_w = sw[(uint32_t)ti * ST + lane];
                     pend_depth = dp;
                     if (cnt <= 1) --top;
-                    else smeta[(size_t)ti * ST + lane] = (uint32_t)dp | ((uint32_t)(cnt - 1) << 16) | ((dirs >> 3) << 19);
+                    else smeta[(uint32_t)ti * ST + lane] = (uint32_t)dp | ((uint32_t)(cnt - 1) << 16) | ((dirs >> 3) << 19);
                     un_lo = dp + 1; un_hi = hi; tour_end = false;
                 }
                 state = kUnwindState;
@@ -506,7 +506,7 @@ __global__ void __launch_bounds__(32 * 9, 1) grow_kernel(const RunDev P) {
 #pragma unroll
             for (int i = 0; i < kUnwind; ++i) {
                 const int k = un_hi - i;
-                if (k >= un_lo) hash[(size_t)sites[(size_t)k * ST + lane] * ST + lane] = (Key)0;
+                if (k >= un_lo) hash[(uint32_t)sites[(uint32_t)k * ST + lane] * ST + lane] = (Key)0;
             }
             un_hi -= kUnwind;
             if (un_hi < un_lo) {
@@ -514,13 +514,13 @@ __global__ void __launch_bounds__(32 * 9, 1) grow_kernel(const RunDev P) {
                     state = kFlush;
                 } else {
                     const int dp = pend_depth;
-                    KeyCodec<D, Key>::decode(hash[(size_t)sites[(size_t)dp * ST + lane] * ST + lane], cx, cy, cz);
+                    KeyCodec<D, Key>::decode(hash[(uint32_t)sites[(uint32_t)dp * ST + lane] * ST + lane], cx, cy, cz);
                     step_coords(pend_dir, cx, cy, cz);
                     n = dp + 1;
                     if (n < P.n_max) {
                         const int s = hash_insert<Key>(hash, ST, lane, P.log2h, KeyCodec<D, Key>::encode(cx, cy, cz));
                         if (s < 0) { set_status(P.status, PERM_EOVERFLOW); state = kDone; }
-                        else sites[(size_t)n * ST + lane] = (uint16_t)s;
+                        else sites[(uint32_t)n * ST + lane] = (uint16_t)s;
                     }
                     W = pend_w;
                     if (state != kDone) state = kNode;
