@@ -71,6 +71,10 @@ typedef struct {
     int ramp_c0;       /* Algorithm 2 admission: at most ramp_c0 + ramp_gamma * (finished
                           tours) tours are in flight.  0 = default (2); < 0 = no limit */
     double ramp_gamma; /* see ramp_c0; 0 = default (1.0) */
+    int max_ctas;      /* at most this many CTAs (SMs) for the run's walks; 0 = all SMs.
+                          Lets concurrent runs share the device */
+    int hash_scale;    /* per-walk occupancy hash has 2^hash_scale * 2 n_max slots
+                          (rounded up to a power of 2); 0..2 */
 } perm_config;
 
 /* Fill cfg with defaults for (d, n_max, n_seq, seed). */
@@ -168,6 +172,33 @@ int perm_debug_step(int d, int n_max, int B, const int32_t *coords, const int32_
                     const uint64_t *ordinal, const uint32_t *seq, const uint32_t *tour,
                     uint64_t seed, uint32_t run_id, int32_t *out_i, float *out_r,
                     double *out_w, uint64_t *out_K, void *stream);
+
+/* ---------------------------------------------------------------------------
+ * Batched runs (many independent runs, one CUDA-graph launch).
+ * perm_batch_create makes R runs (cfgs[r], grown tours_per_seq[r] tours per
+ * sequence from empty tables) and captures all of their work -- table reset,
+ * persistent growth kernel, tour-counter clamp -- into one CUDA graph with one
+ * branch per stream (n_streams; 0 = min(R, 64)).  A run whose cfg.max_ctas is
+ * 0 gets a share of the SMs proportional to n_seq * tours * (n_max + 1).
+ * perm_batch_run replays the graph (every run starts again from empty tables)
+ * and waits; estimates and statistics are then read per run as for a single
+ * handle.  The batch owns its handles, streams and graph.
+ * ------------------------------------------------------------------------- */
+typedef struct perm_batch_s *perm_batch_handle;
+int perm_batch_create(perm_batch_handle *out, const perm_config *cfgs, const int64_t *tours_per_seq,
+                      int R, int n_streams);
+int perm_batch_run(perm_batch_handle b);
+int perm_batch_size(perm_batch_handle b);
+int perm_batch_estimates(perm_batch_handle b, int r, double *log_cn, double *S_n, double *relvar_n);
+int perm_batch_stats(perm_batch_handle b, int r, perm_stats_t *out);
+void perm_batch_destroy(perm_batch_handle b);
+
+/* Autotuner: runs probe_tours of cfg for each walks-per-warp choice (auto, 2,
+ * 4, 8, 16, 32) and hash size (hash_scale 0, 1), and writes the fastest
+ * (growth steps per second) into cfg->lanes_per_warp and cfg->hash_scale.
+ * Results are cached per (d, n_max, n_seq, max_ctas) for the process.
+ * Synchronous; allocates and frees a handle per trial. */
+int perm_autotune(perm_config *cfg, int64_t probe_tours);
 
 /* perm_run_static -- one complete Algorithm-2 growth run that allocates
  * nothing (the paper has no counterpart: this serves callers that cannot

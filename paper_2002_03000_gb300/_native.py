@@ -33,7 +33,8 @@ EXPORTS = (
     "perm_config_init", "perm_create", "perm_create_ex", "perm_set_stream", "perm_run", "perm_reset",
     "perm_run_sync", "perm_estimates", "perm_tables", "perm_stats", "perm_trace_enable",
     "perm_trace_read", "perm_destroy", "perm_strerror", "perm_debug_step", "perm_debug_philox",
-    "perm_run_static",
+    "perm_run_static", "perm_batch_create", "perm_batch_run", "perm_batch_size",
+    "perm_batch_estimates", "perm_batch_stats", "perm_batch_destroy", "perm_autotune",
 )
 
 
@@ -41,7 +42,8 @@ class perm_config(C.Structure):
     _fields_ = [("d", C.c_int), ("n_max", C.c_int), ("n_seq", C.c_int), ("seed", C.c_uint64),
                 ("run_id", C.c_uint32), ("alg", C.c_int), ("threshold", C.c_int),
                 ("slots", C.c_int), ("lanes_per_warp", C.c_int), ("refresh_ns", C.c_int),
-                ("max_seconds", C.c_double), ("ramp_c0", C.c_int), ("ramp_gamma", C.c_double)]
+                ("max_seconds", C.c_double), ("ramp_c0", C.c_int), ("ramp_gamma", C.c_double),
+                ("max_ctas", C.c_int), ("hash_scale", C.c_int)]
 
 
 class perm_stats_t(C.Structure):
@@ -103,8 +105,16 @@ def load(path: str = LIB_PATH):
     L.perm_debug_step.argtypes = [C.c_int, C.c_int, C.c_int] + [vp] * 8 + [u64, u32] + [vp] * 4 + [vp]
     L.perm_debug_philox.argtypes = [C.c_int, vp, C.POINTER(u32), vp]
     L.perm_run_static.argtypes = [C.POINTER(perm_config), i64, vp, vp, vp, C.POINTER(i64), vp]
+    L.perm_batch_create.argtypes = [hp, C.POINTER(perm_config), C.POINTER(i64), C.c_int, C.c_int]
+    L.perm_batch_run.argtypes = [vp]
+    L.perm_batch_size.argtypes = [vp]
+    L.perm_batch_estimates.argtypes = [vp, C.c_int, dp, dp, dp]
+    L.perm_batch_stats.argtypes = [vp, C.c_int, C.POINTER(perm_stats_t)]
+    L.perm_batch_destroy.argtypes = [vp]
+    L.perm_batch_destroy.restype = None
+    L.perm_autotune.argtypes = [C.POINTER(perm_config), i64]
     for name in EXPORTS:
-        if name not in ("perm_config_init", "perm_destroy", "perm_strerror"):
+        if name not in ("perm_config_init", "perm_destroy", "perm_strerror", "perm_batch_destroy"):
             getattr(L, name).restype = C.c_int
     _lib = L
     return L
@@ -217,6 +227,43 @@ def perm_run_static(cfg, tours_per_seq, W_dev, S_dev, Q_dev, stream=0):
     _check(load().perm_run_static(C.byref(cfg), tours_per_seq, W_dev, S_dev, Q_dev,
                                   C.byref(steps), stream), "perm_run_static")
     return steps.value
+
+
+def perm_batch_create(cfgs, tours, n_streams=0):
+    """cfgs: list of perm_config; tours: list of tours per sequence."""
+    R = len(cfgs)
+    arr = (perm_config * R)(*cfgs)
+    t = (C.c_int64 * R)(*[int(x) for x in tours])
+    b = C.c_void_p()
+    _check(load().perm_batch_create(C.byref(b), arr, t, R, n_streams), "perm_batch_create")
+    return b
+
+
+def perm_batch_run(b):
+    _check(load().perm_batch_run(b), "perm_batch_run")
+
+
+def perm_batch_estimates(b, r, n_max):
+    L = n_max + 1
+    lc, S, rv = np.empty(L), np.empty(L), np.empty(L)
+    _check(load().perm_batch_estimates(b, r, _dp(lc), _dp(S), _dp(rv)), "perm_batch_estimates")
+    return lc, S, rv
+
+
+def perm_batch_stats(b, r):
+    st = perm_stats_t()
+    _check(load().perm_batch_stats(b, r, C.byref(st)), "perm_batch_stats")
+    return {name: getattr(st, name) for name, _ in perm_stats_t._fields_}
+
+
+def perm_batch_destroy(b):
+    if b:
+        load().perm_batch_destroy(b)
+
+
+def perm_autotune(cfg, probe_tours):
+    _check(load().perm_autotune(C.byref(cfg), probe_tours), "perm_autotune")
+    return cfg
 
 
 def perm_debug_philox(B, ctr_dev, key, out_dev):

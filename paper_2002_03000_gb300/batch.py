@@ -1,0 +1,73 @@
+"""Batched flatPERM runs: many independent runs grown by one CUDA-graph launch.
+
+Thin wrapper of perm_batch_* (include/perm.h); the runs' growth happens in the
+persistent CUDA kernel, the graph is captured and replayed by the library.
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+from . import _native as nat
+
+
+class Batch:
+    """R independent runs; run() replays the captured graph (fresh tables)."""
+
+    def __init__(self, configs, tours, n_streams=0):
+        self.configs = list(configs)
+        self.tours = [int(t) for t in tours]
+        self.b = nat.perm_batch_create(self.configs, self.tours, n_streams)
+
+    def run(self):
+        nat.perm_batch_run(self.b)
+
+    def estimates(self, r):
+        return nat.perm_batch_estimates(self.b, r, self.configs[r].n_max)
+
+    def stats(self, r):
+        return nat.perm_batch_stats(self.b, r)
+
+    def close(self):
+        if self.b:
+            nat.perm_batch_destroy(self.b)
+            self.b = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def make_config(d, n_max, n_seq, seed, run_id=0, **kw):
+    cfg = nat.perm_config_init(d, n_max, n_seq, seed)
+    cfg.run_id = run_id
+    for k, v in kw.items():
+        setattr(cfg, k, v)
+    return cfg
+
+
+def mixed_runs(count=96, seed=1, n_max_range=(64, 2048), n_seq_range=(256, 8192)):
+    """Seeded workload of independent runs: d uniform in {2, 3}, n_max and the
+    number of sequences log-uniform in the given ranges (PCG64)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    out = []
+    for r in range(count):
+        d = int(rng.integers(2, 4))
+        n_max = int(round(math.exp(rng.uniform(math.log(n_max_range[0]), math.log(n_max_range[1])))))
+        n_seq = int(round(math.exp(rng.uniform(math.log(n_seq_range[0]), math.log(n_seq_range[1])))))
+        out.append((d, n_max, n_seq))
+    return out
+
+
+def autotune(cfg, probe_tours=2):
+    """Pick walks per warp and hash size for cfg by short calibration runs."""
+    return nat.perm_autotune(cfg, probe_tours)

@@ -12,7 +12,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libperm.so")
-SOURCES = ["perm_kernels.cu", "perm_capi.cu", "perm_noalloc.cu"]
+SOURCES = ["perm_kernels.cu", "perm_capi.cu", "perm_noalloc.cu", "perm_batch.cu"]
 HEADERS = ["perm_device.cuh", "perm_kernels.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "--fmad=false", "-Xcompiler", "-fPIC",

@@ -1,0 +1,216 @@
+// perm_batch.cu -- many independent flatPERM runs grown by one CUDA-graph launch,
+// and the autotuner that picks each run's layout.
+//
+// A batch holds R runs (each a perm_handle with its own tables and stream).
+// Their work -- reset of the tables, the persistent growth kernel, the tour
+// counter clamp -- is captured once into a CUDA graph with one branch per
+// stream.  Replaying the graph grows every run again from empty tables; the
+// branches run concurrently, each run's kernel limited to a share of the SMs
+// proportional to its expected work (sequences x tours x (n_max + 1)), so that
+// small runs fill the device together instead of one after another.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <new>
+#include <tuple>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "perm.h"
+#include "perm_kernels.cuh"
+
+struct perm_batch_s {
+    int R = 0;
+    std::vector<perm_handle> runs;
+    std::vector<int64_t> tours;
+    std::vector<cudaStream_t> streams;
+    std::vector<cudaEvent_t> joins;
+    cudaStream_t origin = nullptr;
+    cudaEvent_t fork = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+};
+
+namespace {
+
+void batch_free(perm_batch_handle b) {
+    if (!b) return;
+    if (b->origin) cudaStreamSynchronize(b->origin);
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (b->graph) cudaGraphDestroy(b->graph);
+    for (perm_handle h : b->runs) perm_destroy(h);
+    for (cudaEvent_t e : b->joins) cudaEventDestroy(e);
+    if (b->fork) cudaEventDestroy(b->fork);
+    for (cudaStream_t s : b->streams) cudaStreamDestroy(s);
+    if (b->origin) cudaStreamDestroy(b->origin);
+    delete b;
+}
+
+}  // namespace
+
+extern "C" {
+
+int perm_batch_create(perm_batch_handle *out, const perm_config *cfgs, const int64_t *tours_per_seq,
+                      int R, int n_streams) {
+    if (!out || !cfgs || !tours_per_seq || R < 1) return PERM_EINVAL;
+    *out = nullptr;
+    for (int r = 0; r < R; ++r)
+        if (tours_per_seq[r] < 0) return PERM_EINVAL;
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+        return PERM_EDEVICE;
+    if (perm::set_smem_limits() != cudaSuccess) return PERM_EDEVICE;
+    perm_batch_handle b = new (std::nothrow) perm_batch_s();
+    if (!b) return PERM_ENOMEM;
+    b->R = R;
+    b->tours.assign(tours_per_seq, tours_per_seq + R);
+
+    // share of the SMs per run, proportional to its expected work
+    std::vector<double> work(R);
+    double total = 0.0;
+    for (int r = 0; r < R; ++r) {
+        work[r] = (double)cfgs[r].n_seq * (double)tours_per_seq[r] * (double)(cfgs[r].n_max + 1);
+        total += work[r];
+    }
+    int S = n_streams > 0 ? n_streams : std::min(R, 64);
+    S = std::min(S, R);
+    int rc = PERM_OK;
+    if (cudaStreamCreateWithFlags(&b->origin, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming) != cudaSuccess)
+        rc = PERM_EDEVICE;
+    for (int s = 0; rc == PERM_OK && s < S; ++s) {
+        cudaStream_t st;
+        cudaEvent_t ev;
+        if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) { rc = PERM_EDEVICE; break; }
+        b->streams.push_back(st);
+        if (cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess) { rc = PERM_EDEVICE; break; }
+        b->joins.push_back(ev);
+    }
+    for (int r = 0; rc == PERM_OK && r < R; ++r) {
+        perm_config c = cfgs[r];
+        if (c.max_ctas == 0 && total > 0.0) {
+            const int share = (int)std::ceil((double)sms * work[r] / total);
+            c.max_ctas = std::max(1, std::min(sms, share));
+        }
+        perm_handle h = nullptr;
+        rc = perm_create_ex(&h, &c);
+        if (rc != PERM_OK) break;
+        b->runs.push_back(h);
+        rc = perm_set_stream(h, (void *)b->streams[r % S]);
+    }
+    // capture: fork to the run streams, reset + grow each run, join
+    if (rc == PERM_OK && cudaStreamBeginCapture(b->origin, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
+        rc = PERM_EDEVICE;
+    if (rc == PERM_OK) {
+        cudaError_t e = cudaEventRecord(b->fork, b->origin);
+        for (int s = 0; e == cudaSuccess && s < S; ++s) e = cudaStreamWaitEvent(b->streams[s], b->fork, 0);
+        if (e != cudaSuccess) rc = PERM_EDEVICE;
+        for (int r = 0; rc == PERM_OK && r < R; ++r) {
+            rc = perm_reset(b->runs[r]);
+            if (rc == PERM_OK) rc = perm_run(b->runs[r], b->tours[r]);
+        }
+        for (int s = 0; rc == PERM_OK && s < S; ++s) {
+            if (cudaEventRecord(b->joins[s], b->streams[s]) != cudaSuccess ||
+                cudaStreamWaitEvent(b->origin, b->joins[s], 0) != cudaSuccess)
+                rc = PERM_EDEVICE;
+        }
+        cudaGraph_t g = nullptr;
+        const cudaError_t ec = cudaStreamEndCapture(b->origin, &g);
+        if (rc == PERM_OK && ec != cudaSuccess) rc = PERM_EDEVICE;
+        b->graph = g;
+        if (rc == PERM_OK && cudaGraphInstantiate(&b->exec, b->graph, 0) != cudaSuccess) rc = PERM_EDEVICE;
+    }
+    if (rc != PERM_OK) {
+        batch_free(b);
+        return rc;
+    }
+    *out = b;
+    return PERM_OK;
+}
+
+int perm_batch_run(perm_batch_handle b) {
+    if (!b || !b->exec) return PERM_EINVAL;
+    if (cudaGraphLaunch(b->exec, b->origin) != cudaSuccess) return PERM_EDEVICE;
+    if (cudaStreamSynchronize(b->origin) != cudaSuccess) return PERM_EDEVICE;
+    for (perm_handle h : b->runs) {
+        perm_stats_t st;
+        const int rc = perm_stats(h, &st);
+        if (rc != PERM_OK) return rc;
+        if (st.status != PERM_OK) return st.status;
+    }
+    return PERM_OK;
+}
+
+int perm_batch_size(perm_batch_handle b) { return b ? b->R : PERM_EINVAL; }
+
+int perm_batch_estimates(perm_batch_handle b, int r, double *log_cn, double *S_n, double *relvar_n) {
+    if (!b || r < 0 || r >= b->R) return PERM_EINVAL;
+    return perm_estimates(b->runs[r], log_cn, S_n, relvar_n);
+}
+
+int perm_batch_stats(perm_batch_handle b, int r, perm_stats_t *out) {
+    if (!b || r < 0 || r >= b->R) return PERM_EINVAL;
+    return perm_stats(b->runs[r], out);
+}
+
+void perm_batch_destroy(perm_batch_handle b) { batch_free(b); }
+
+// ---------------------------------------------------------------------------
+// Autotuner: short calibration runs over walks per warp and hash size; the
+// best configuration (growth steps per second) is written back and cached per
+// (d, n_max, n_seq, max_ctas).
+// ---------------------------------------------------------------------------
+namespace {
+std::mutex g_tune_mutex;
+std::map<std::tuple<int, int, int, int>, std::pair<int, int>> g_tune_cache;
+}  // namespace
+
+int perm_autotune(perm_config *cfg, int64_t probe_tours) {
+    if (!cfg || probe_tours < 1) return PERM_EINVAL;
+    const auto key = std::make_tuple(cfg->d, cfg->n_max, cfg->n_seq, cfg->max_ctas);
+    {
+        std::lock_guard<std::mutex> lock(g_tune_mutex);
+        auto it = g_tune_cache.find(key);
+        if (it != g_tune_cache.end()) {
+            cfg->lanes_per_warp = it->second.first;
+            cfg->hash_scale = it->second.second;
+            return PERM_OK;
+        }
+    }
+    const int lanes_c[] = {0, 2, 4, 8, 16, 32};
+    const int hash_c[] = {0, 1};
+    double best = -1.0;
+    int best_l = 0, best_h = 0;
+    for (int hs : hash_c) {
+        for (int lw : lanes_c) {
+            perm_config c = *cfg;
+            c.lanes_per_warp = lw;
+            c.hash_scale = hs;
+            perm_handle h = nullptr;
+            if (perm_create_ex(&h, &c) != PERM_OK) continue;
+            perm_stats_t st;
+            const auto t0 = std::chrono::steady_clock::now();
+            const int rc = perm_run_sync(h, probe_tours);
+            const auto t1 = std::chrono::steady_clock::now();
+            if (rc == PERM_OK && perm_stats(h, &st) == PERM_OK) {
+                const double sec = std::chrono::duration<double>(t1 - t0).count();
+                const double rate = (double)st.steps / (sec > 0 ? sec : 1e-9);
+                if (rate > best) { best = rate; best_l = lw; best_h = hs; }
+            }
+            perm_destroy(h);
+        }
+    }
+    if (best < 0.0) return PERM_EUNSUPPORTED;
+    cfg->lanes_per_warp = best_l;
+    cfg->hash_scale = best_h;
+    std::lock_guard<std::mutex> lock(g_tune_mutex);
+    g_tune_cache[key] = std::make_pair(best_l, best_h);
+    return PERM_OK;
+}
+
+}  // extern "C"

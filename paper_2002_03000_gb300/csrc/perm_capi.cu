@@ -98,6 +98,8 @@ void perm_config_init(perm_config *cfg, int d, int n_max, int n_seq, uint64_t se
     cfg->max_seconds = 0.0;
     cfg->ramp_c0 = 0;
     cfg->ramp_gamma = 0.0;
+    cfg->max_ctas = 0;
+    cfg->hash_scale = 0;
 }
 
 const char *perm_strerror(int code) {
@@ -123,6 +125,7 @@ int perm_create_ex(perm_handle *out, const perm_config *cfg) {
     if (cfg->threshold != PERM_THRESH_SNAPSHOT && cfg->threshold != PERM_THRESH_FRESH) return PERM_EINVAL;
     if (cfg->slots < 0 || cfg->refresh_ns < 0 || !(cfg->max_seconds >= 0.0)) return PERM_EINVAL;
     if (!(cfg->ramp_gamma >= 0.0) || cfg->ramp_gamma > 1e6) return PERM_EINVAL;
+    if (cfg->max_ctas < 0 || cfg->hash_scale < 0 || cfg->hash_scale > 2) return PERM_EINVAL;
     const int lpw = cfg->lanes_per_warp;
     if (lpw != 0 && (lpw < 1 || lpw > 32)) return PERM_EINVAL;
     const bool key64 = (d == 3 && n_max > 512);
@@ -143,12 +146,15 @@ int perm_create_ex(perm_handle *out, const perm_config *cfg) {
     if (h->cfg.ramp_gamma == 0.0) h->cfg.ramp_gamma = 1.0;
     h->device = dev;
     h->num_sms = prop.multiProcessorCount;
+    if (cfg->max_ctas > 0 && cfg->max_ctas < h->num_sms) h->num_sms = cfg->max_ctas;
     h->key64 = key64;
     // Algorithm 1 reads its private rows directly (no snapshot needed)
     h->thresh = (cfg->alg == PERM_ALG1) ? perm::kFresh
               : (cfg->threshold == PERM_THRESH_FRESH ? perm::kFresh : perm::kSnapshot);
     int log2h = 4;
     while ((1 << log2h) < 2 * n_max) ++log2h;
+    log2h += cfg->hash_scale;
+    if (log2h > 16) log2h = 16;                 // site slots are 16-bit
     h->log2h = log2h;
     if (cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking) != cudaSuccess) {
         delete h;
@@ -295,11 +301,19 @@ int perm_run(perm_handle h, int64_t tours_per_seq) {
     return PERM_OK;
 }
 
+// Copy device -> host on the handle's own stream and wait for that stream only
+// (other streams, e.g. other runs served concurrently, keep running).
+static cudaError_t copy_out(perm_handle h, void *dst, const void *src, size_t bytes) {
+    cudaError_t e = cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    return e;
+}
+
 static int sync_status(perm_handle h) {
     cudaError_t e = cudaStreamSynchronize(h->stream);
     if (e != cudaSuccess) return to_code(e);
     int st = 0;
-    e = cudaMemcpy(&st, h->status, sizeof(int), cudaMemcpyDeviceToHost);
+    e = copy_out(h, &st, h->status, sizeof(int));
     if (e != cudaSuccess) return to_code(e);
     h->last_status = st;
     return st;
@@ -317,11 +331,11 @@ int perm_tables(perm_handle h, double *W_n, double *S_n, double *Q_n, int64_t *M
     if (st < 0 && st != PERM_EOVERFLOW && st != PERM_ETIMEOUT) return st;
     const size_t L = (size_t)h->cfg.n_max + 1, cnt = L * h->ntab;
     cudaError_t e = cudaSuccess;
-    if (W_n) e = cudaMemcpy(W_n, h->Wn, cnt * sizeof(double), cudaMemcpyDeviceToHost);
-    if (e == cudaSuccess && Q_n) e = cudaMemcpy(Q_n, h->Qn, cnt * sizeof(double), cudaMemcpyDeviceToHost);
+    if (W_n) e = copy_out(h, W_n, h->Wn, cnt * sizeof(double));
+    if (e == cudaSuccess && Q_n) e = copy_out(h, Q_n, h->Qn, cnt * sizeof(double));
     if (e == cudaSuccess && S_n) {
         std::vector<unsigned long long> s(cnt);
-        e = cudaMemcpy(s.data(), h->Sn, cnt * sizeof(unsigned long long), cudaMemcpyDeviceToHost);
+        e = copy_out(h, s.data(), h->Sn, cnt * sizeof(unsigned long long));
         for (size_t i = 0; i < cnt; ++i) S_n[i] = (double)s[i];
     }
     if (e == cudaSuccess && M) {
@@ -329,7 +343,7 @@ int perm_tables(perm_handle h, double *W_n, double *S_n, double *Q_n, int64_t *M
             M[0] = h->tour_limit;
         } else {
             std::vector<unsigned long long> m(h->cfg.n_seq);
-            e = cudaMemcpy(m.data(), h->seq_M, m.size() * sizeof(unsigned long long), cudaMemcpyDeviceToHost);
+            e = copy_out(h, m.data(), h->seq_M, m.size() * sizeof(unsigned long long));
             for (size_t i = 0; i < m.size(); ++i) M[i] = (int64_t)m[i];
         }
     }
@@ -396,11 +410,11 @@ int perm_stats(perm_handle h, perm_stats_t *out) {
     int st = sync_status(h);
     if (st < 0 && st != PERM_EOVERFLOW && st != PERM_ETIMEOUT) return st;
     unsigned long long steps = 0, ms = 0, cp = 0, rf = 0, it = 0;
-    if (cudaMemcpy(&steps, h->steps, 8, cudaMemcpyDeviceToHost) != cudaSuccess) return PERM_EDEVICE;
-    if (cudaMemcpy(&cp, h->copies, 8, cudaMemcpyDeviceToHost) != cudaSuccess) return PERM_EDEVICE;
-    if (cudaMemcpy(&rf, h->refreshes, 8, cudaMemcpyDeviceToHost) != cudaSuccess) return PERM_EDEVICE;
-    if (cudaMemcpy(&it, h->iterations, 8, cudaMemcpyDeviceToHost) != cudaSuccess) return PERM_EDEVICE;
-    if (cudaMemcpy(&ms, h->max_stack, 8, cudaMemcpyDeviceToHost) != cudaSuccess) return PERM_EDEVICE;
+    if (copy_out(h, &steps, h->steps, 8) != cudaSuccess) return PERM_EDEVICE;
+    if (copy_out(h, &cp, h->copies, 8) != cudaSuccess) return PERM_EDEVICE;
+    if (copy_out(h, &rf, h->refreshes, 8) != cudaSuccess) return PERM_EDEVICE;
+    if (copy_out(h, &it, h->iterations, 8) != cudaSuccess) return PERM_EDEVICE;
+    if (copy_out(h, &ms, h->max_stack, 8) != cudaSuccess) return PERM_EDEVICE;
     out->steps = (int64_t)steps;
     out->tours = h->cfg.alg == PERM_ALG2 ? h->tour_limit : h->seq_target * h->cfg.n_seq;
     out->max_stack = (int64_t)ms;

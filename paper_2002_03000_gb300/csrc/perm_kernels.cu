@@ -659,18 +659,41 @@ size_t cta_smem_bytes(int d, bool key64, int n_max, int log2h, int stack_cache, 
 
 namespace {
 template <int D, typename Key, int MODE>
+cudaError_t allow_smem() {
+    // the largest opt-in shared memory per block, set once per instantiation
+    static int done = 0;
+    if (done) return cudaSuccess;
+    int dev = 0, optin = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(grow_kernel<D, Key, MODE>,
+                                                   cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
+    if (e == cudaSuccess) done = 1;
+    return e;
+}
+
+template <int D, typename Key, int MODE>
 cudaError_t launch_one(const RunDev &P, int ctas, cudaStream_t stream) {
     const bool snapshot = (MODE == kSnapshot);
     const size_t smem = cta_smem_bytes(D, sizeof(Key) == 8, P.n_max, P.log2h, P.stack_cache,
                                        P.worker_warps, snapshot, P.stride);
-    cudaError_t e = cudaFuncSetAttribute(grow_kernel<D, Key, MODE>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = allow_smem<D, Key, MODE>();
     if (e != cudaSuccess) return e;
     const int threads = 32 * (P.worker_warps + (snapshot ? 1 : 0));
     grow_kernel<D, Key, MODE><<<ctas, threads, smem, stream>>>(P);
     return cudaGetLastError();
 }
 }  // namespace
+
+cudaError_t set_smem_limits() {
+    cudaError_t e = allow_smem<2, uint32_t, kSnapshot>();
+    if (e == cudaSuccess) e = allow_smem<2, uint32_t, kFresh>();
+    if (e == cudaSuccess) e = allow_smem<3, uint32_t, kSnapshot>();
+    if (e == cudaSuccess) e = allow_smem<3, uint32_t, kFresh>();
+    if (e == cudaSuccess) e = allow_smem<3, unsigned long long, kSnapshot>();
+    if (e == cudaSuccess) e = allow_smem<3, unsigned long long, kFresh>();
+    return e;
+}
 
 cudaError_t launch_grow(const RunDev &P, int thresh_mode, bool key64, int ctas, cudaStream_t stream) {
     if (P.d == 2) {
