@@ -75,6 +75,11 @@ typedef struct {
                           Lets concurrent runs share the device */
     int hash_scale;    /* per-walk occupancy hash has 2^hash_scale * 2 n_max slots
                           (rounded up to a power of 2); 0..2 */
+    int share_copies;  /* Algorithm 2 with snapshot thresholds: a walk with no tour to
+                          start (admission limit, or no tickets left) takes the oldest
+                          waiting copy of another walk's tour and grows its subtree; the
+                          copy's weights still count for that tour (Sec. 2: the copies
+                          grow independently).  0 = on (default), -1 = off */
 } perm_config;
 
 /* Fill cfg with defaults for (d, n_max, n_seq, seed). */
@@ -130,6 +135,8 @@ typedef struct {
     int hash_slots;       /* per-walk occupancy hash size */
     int status;           /* PERM_OK or the device-side error of the last run */
     int64_t device_bytes; /* device memory held by the handle */
+    int64_t tours_finished; /* tours whose copies have all been grown, cumulative */
+    int64_t shared;       /* waiting copies handed to other walks, cumulative */
 } perm_stats_t;
 int perm_stats(perm_handle h, perm_stats_t *out);
 

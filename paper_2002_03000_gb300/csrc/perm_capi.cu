@@ -34,6 +34,13 @@ struct perm_run_s {
     unsigned long long *iterations = nullptr, *finished = nullptr;
     uint32_t *gstk_meta = nullptr;
     int *status = nullptr;
+    // shared copies
+    bool share = false;
+    int dq_log2cap = 0, dq_cell_bytes = 0;
+    unsigned char *dq_cells = nullptr;
+    unsigned long long *dq_head = nullptr, *dq_tail = nullptr;
+    unsigned int *dq_ready = nullptr, *dq_free = nullptr, *outst = nullptr, *tmaxn = nullptr;
+    int *hungry = nullptr;
     perm_trace_record *trace = nullptr;
     int32_t *trace_coords = nullptr;
     int trace_cap = 0;
@@ -67,7 +74,8 @@ int dalloc(perm_handle h, T **p, size_t count) {
 void free_all(perm_handle h) {
     void *ptrs[] = {h->Wn, h->Qn, h->X, h->gstk_w, h->Sn, h->tickets, h->seq_M, h->steps,
                     h->max_stack, h->copies, h->refreshes, h->iterations, h->finished, h->trace_count, h->gstk_meta, h->status, h->trace,
-                    h->trace_coords};
+                    h->trace_coords, h->dq_cells, h->dq_head, h->dq_tail, h->dq_ready, h->dq_free, h->outst,
+                    h->tmaxn, h->hungry};
     for (void *p : ptrs) if (p) cudaFree(p);
 }
 
@@ -100,6 +108,7 @@ void perm_config_init(perm_config *cfg, int d, int n_max, int n_seq, uint64_t se
     cfg->ramp_gamma = 0.0;
     cfg->max_ctas = 0;
     cfg->hash_scale = 0;
+    cfg->share_copies = 0;
 }
 
 const char *perm_strerror(int code) {
@@ -126,6 +135,7 @@ int perm_create_ex(perm_handle *out, const perm_config *cfg) {
     if (cfg->slots < 0 || cfg->refresh_ns < 0 || !(cfg->max_seconds >= 0.0)) return PERM_EINVAL;
     if (!(cfg->ramp_gamma >= 0.0) || cfg->ramp_gamma > 1e6) return PERM_EINVAL;
     if (cfg->max_ctas < 0 || cfg->hash_scale < 0 || cfg->hash_scale > 2) return PERM_EINVAL;
+    if (cfg->share_copies != 0 && cfg->share_copies != -1) return PERM_EINVAL;
     const int lpw = cfg->lanes_per_warp;
     if (lpw != 0 && (lpw < 1 || lpw > 32)) return PERM_EINVAL;
     const bool key64 = (d == 3 && n_max > 512);
@@ -227,6 +237,25 @@ int perm_create_ex(perm_handle *out, const perm_config *cfg) {
     if (rc == PERM_OK) rc = dalloc(h, &h->finished, 1);
     if (rc == PERM_OK) rc = dalloc(h, &h->trace_count, 1);
     if (rc == PERM_OK) rc = dalloc(h, &h->status, 1);
+    // shared copies: a ring of cells, each one waiting copy record plus the keys of the
+    // walk up to its branch point
+    h->share = cfg->share_copies == 0 && cfg->alg == PERM_ALG2 && h->thresh == perm::kSnapshot;
+    if (rc == PERM_OK && h->share) {
+        int lc = 6;
+        while ((1 << lc) < h->slots && lc < 12) ++lc;
+        h->dq_log2cap = lc;
+        h->dq_cell_bytes = (int)(32 + ((((size_t)n_max + 1) * (key64 ? 8 : 4) + 15) & ~(size_t)15));
+        const size_t cap = (size_t)1 << lc;
+        rc = dalloc(h, &h->dq_cells, cap * (size_t)h->dq_cell_bytes);
+        if (rc == PERM_OK) rc = dalloc(h, &h->dq_ready, cap);
+        if (rc == PERM_OK) rc = dalloc(h, &h->dq_free, cap);
+        if (rc == PERM_OK) rc = dalloc(h, &h->dq_head, 1);
+        if (rc == PERM_OK) rc = dalloc(h, &h->dq_tail, 1);
+        if (rc == PERM_OK) rc = dalloc(h, &h->outst, (size_t)h->slots);
+        if (rc == PERM_OK) rc = to_code(cudaMemsetAsync(h->outst, 0xFF, sizeof(unsigned int) * h->slots, h->stream));
+        if (rc == PERM_OK) rc = dalloc(h, &h->tmaxn, (size_t)h->slots);
+        if (rc == PERM_OK) rc = dalloc(h, &h->hungry, 1);
+    }
     if (rc == PERM_OK) rc = to_code(cudaStreamSynchronize(h->stream));
     if (rc != PERM_OK) {
         free_all(h);
@@ -272,6 +301,10 @@ static RunDev make_params(perm_handle h) {
     P.finished = h->finished;
     P.ramp_c0 = h->cfg.ramp_c0 < 0 ? -1 : (long long)h->cfg.ramp_c0;
     P.ramp_gamma_q16 = (unsigned long long)(h->cfg.ramp_gamma * 65536.0);
+    P.share = h->share ? 1 : 0;
+    P.dq_log2cap = h->dq_log2cap; P.dq_cell_bytes = h->dq_cell_bytes; P.dq_cells = h->dq_cells;
+    P.dq_head = h->dq_head; P.dq_tail = h->dq_tail; P.dq_ready = h->dq_ready; P.dq_free = h->dq_free;
+    P.outst = h->outst; P.tmaxn = h->tmaxn; P.hungry = h->hungry;
     P.status = h->status;
     P.trace = (h->trace_every > 0) ? h->trace : nullptr;
     P.trace_coords = h->trace_coords; P.trace_count = h->trace_count; P.trace_cap = h->trace_cap;
@@ -368,6 +401,16 @@ int perm_reset(perm_handle h) {
     if (e == cudaSuccess) e = cudaMemsetAsync(h->status, 0, sizeof(int), h->stream);
     if (e == cudaSuccess && h->last_status != PERM_OK)   // a stopped run may leave tour sums behind
         e = cudaMemsetAsync(h->X, 0, L * (size_t)h->slots * sizeof(double), h->stream);
+    if (e == cudaSuccess && h->share) {
+        const size_t cap = (size_t)1 << h->dq_log2cap;
+        e = cudaMemsetAsync(h->dq_head, 0, sizeof(unsigned long long), h->stream);
+        if (e == cudaSuccess) e = cudaMemsetAsync(h->dq_tail, 0, sizeof(unsigned long long), h->stream);
+        if (e == cudaSuccess) e = cudaMemsetAsync(h->dq_ready, 0, sizeof(unsigned int) * cap, h->stream);
+        if (e == cudaSuccess) e = cudaMemsetAsync(h->dq_free, 0, sizeof(unsigned int) * cap, h->stream);
+        if (e == cudaSuccess) e = cudaMemsetAsync(h->hungry, 0, sizeof(int), h->stream);
+        if (e == cudaSuccess) e = cudaMemsetAsync(h->outst, 0xFF, sizeof(unsigned int) * h->slots, h->stream);
+        if (e == cudaSuccess) e = cudaMemsetAsync(h->tmaxn, 0, sizeof(unsigned int) * h->slots, h->stream);
+    }
     if (e != cudaSuccess) return to_code(e);
     h->tour_limit = 0;
     h->seq_target = 0;
@@ -409,12 +452,14 @@ int perm_stats(perm_handle h, perm_stats_t *out) {
     if (!h || !out) return PERM_EINVAL;
     int st = sync_status(h);
     if (st < 0 && st != PERM_EOVERFLOW && st != PERM_ETIMEOUT) return st;
-    unsigned long long steps = 0, ms = 0, cp = 0, rf = 0, it = 0;
+    unsigned long long steps = 0, ms = 0, cp = 0, rf = 0, it = 0, fin = 0, shr = 0;
     if (copy_out(h, &steps, h->steps, 8) != cudaSuccess) return PERM_EDEVICE;
     if (copy_out(h, &cp, h->copies, 8) != cudaSuccess) return PERM_EDEVICE;
     if (copy_out(h, &rf, h->refreshes, 8) != cudaSuccess) return PERM_EDEVICE;
     if (copy_out(h, &it, h->iterations, 8) != cudaSuccess) return PERM_EDEVICE;
     if (copy_out(h, &ms, h->max_stack, 8) != cudaSuccess) return PERM_EDEVICE;
+    if (copy_out(h, &fin, h->finished, 8) != cudaSuccess) return PERM_EDEVICE;
+    if (h->share && copy_out(h, &shr, h->dq_tail, 8) != cudaSuccess) return PERM_EDEVICE;
     out->steps = (int64_t)steps;
     out->tours = h->cfg.alg == PERM_ALG2 ? h->tour_limit : h->seq_target * h->cfg.n_seq;
     out->max_stack = (int64_t)ms;
@@ -428,6 +473,8 @@ int perm_stats(perm_handle h, perm_stats_t *out) {
     out->hash_slots = 1 << h->log2h;
     out->status = st;
     out->device_bytes = h->device_bytes;
+    out->tours_finished = (int64_t)fin;
+    out->shared = (int64_t)shr;
     return PERM_OK;
 }
 

@@ -30,6 +30,9 @@ namespace {
 constexpr int kStride = 32;        // interleave stride of the snapshot-state kernel
 constexpr int kUnwind = 8;         // hash deletions per walk per iteration
 constexpr int kPoolExtra = 4;      // extra tour tickets fetched per warp (snapshot)
+constexpr unsigned kRowFree = 0xFFFFFFFFu;   // outst: the walk's tour-sum row is unused
+constexpr int kMinShareGap = 8;    // share a waiting copy only if it may still grow this many steps
+constexpr int kCellSpin = 1 << 20; // bounded wait for a donation cell being written
 constexpr unsigned kFull = 0xFFFFFFFFu;
 
 enum LaneState { kNeed = 0, kNode = 1, kUnwindState = 2, kFlush = 3, kDone = 4 };
@@ -38,9 +41,20 @@ enum Outcome { kLeafNmax = 0, kTrapped = 1, kPruned = 2, kChildren = 3 };
 struct CtaHead {
     unsigned long long Ms;   // tours started, as of the last snapshot
     int done_warps;
-    int pad[13];
+    int want_don;            // copies this CTA may still hand to idle walks this period
+    int queued;              // shared copies waiting in the ring, as of the last snapshot
+    int status;              // run status, as of the last snapshot
+    unsigned long long fin;  // tours finished, as of the last snapshot
+    int pad[8];
 };
 static_assert(sizeof(CtaHead) == 64, "header size");
+
+// A 16-byte vector of occupancy keys (the walk of a shared copy is moved in these).
+template <typename Key> constexpr int kKeysPerVec = 16 / (int)sizeof(Key);
+template <typename Key> union KeyVec {
+    uint4 v;
+    Key k[16 / sizeof(Key)];
+};
 
 __device__ __forceinline__ long long global_ns() {
     long long t;
@@ -223,6 +237,19 @@ __global__ void __launch_bounds__(32 * 9, 1) grow_kernel(const RunDev P) {
                 *(volatile unsigned long long *)&Tpack[k] = pack_threshold(__dmul_rn(Wg, invM));
             }
             if (lane == 0) *(volatile unsigned long long *)&head->Ms = Ms;
+            if (P.share && lane == 0) {
+                // idle walks not yet served by a queued copy, split over the CTAs
+                const long long hg = *(volatile int *)P.hungry;
+                long long q = (long long)(*(volatile unsigned long long *)P.dq_tail -
+                                          *(volatile unsigned long long *)P.dq_head);
+                q = q < 0 ? 0 : (q > (1 << 30) ? (1 << 30) : q);
+                const long long want = hg - q;
+                const long long per = want > 0 ? (want + gridDim.x - 1) / gridDim.x : 0;
+                *(volatile int *)&head->want_don = (int)(per < (1 << 20) ? per : (1 << 20));
+                *(volatile int *)&head->queued = (int)q;
+                *(volatile int *)&head->status = *(volatile int *)P.status;
+                *(volatile unsigned long long *)&head->fin = *(volatile unsigned long long *)P.finished;
+            }
             __syncwarp();
             __nanosleep((unsigned)P.refresh_ns);
             const bool late = (it & 15) == 0 && global_ns() - t0 > P.max_ns;
@@ -250,7 +277,6 @@ __global__ void __launch_bounds__(32 * 9, 1) grow_kernel(const RunDev P) {
     const int slot = gwarp * P.S + lane;
     const bool active = lane < P.S && slot < P.slots;
     const int sidx = active ? slot : 0;
-    double *Xrow = P.X + (size_t)sidx * L;
     uint32_t *gmeta = P.gstk_meta + (size_t)sidx * P.n_max;
     double *gwt = P.gstk_w + (size_t)sidx * P.n_max;
     const unsigned lt_mask = (1u << lane) - 1u;
@@ -272,6 +298,18 @@ __global__ void __launch_bounds__(32 * 9, 1) grow_kernel(const RunDev P) {
     long long seq_t = 0;
     unsigned long long pool_lo = 0ull, pool_hi = 0ull;
     bool waiting = false;
+    // shared copies: the walk grows either its own tour or a part of another
+    // walk's tour (own = that walk's slot, did = the part's donation id)
+    int own = sidx, bot = 0;
+    uint32_t did = 0u;
+    bool donated = false;      // a part of this walk's own tour went to another walk
+    bool xbusy = false;        // this walk's tour-sum row is still used by such a part
+    bool exhausted = false;    // no tour tickets left in this launch
+    int my_hungry = 0;         // lane 0: this warp's share of P.hungry
+    unsigned idle_ns = 500u;   // back-off of a warp with nothing to grow
+    int frow = 0, fmaxn = 0;   // tour-sum row to flush at a part's end, and its depth
+    bool do_flush = false, shared_flush = false;
+    const uint32_t dq_mask = (1u << P.dq_log2cap) - 1u;
     unsigned long long my_iters = 0ull;
     double *Wrow = P.Wn;
     unsigned long long *Srow = P.Sn;
@@ -284,7 +322,9 @@ __global__ void __launch_bounds__(32 * 9, 1) grow_kernel(const RunDev P) {
             break;
         }
         // ---------------- tour tickets ----------------
-        const unsigned need = __ballot_sync(kFull, state == kNeed);
+        if (state == kNeed && xbusy && *(volatile unsigned int *)(P.outst + sidx) == kRowFree) xbusy = false;
+        const bool want_t = state == kNeed && !xbusy && !exhausted;
+        const unsigned need = __ballot_sync(kFull, want_t);
         if (need) {
             if (P.alg == PERM_ALG2) {
                 const unsigned cnt = __popc(need);
@@ -325,7 +365,7 @@ __global__ void __launch_bounds__(32 * 9, 1) grow_kernel(const RunDev P) {
                     take = __shfl_sync(kFull, take, leader);
                 }
                 const bool served = rank < avail + take;
-                if (state == kNeed && served) g = (rank < avail) ? pool_lo + rank : base + (rank - avail);
+                if (want_t && served) g = (rank < avail) ? pool_lo + rank : base + (rank - avail);
                 if (avail >= cnt) {
                     pool_lo += cnt;
                 } else if (avail + take > cnt) {
@@ -334,12 +374,13 @@ __global__ void __launch_bounds__(32 * 9, 1) grow_kernel(const RunDev P) {
                 } else {
                     pool_lo = pool_hi = 0ull;      // pool and grant all handed out
                 }
-                if (state == kNeed && !served) {
+                if (want_t && !served) {
                     waiting = true;                // not admitted yet: try again next round
-                } else if (state == kNeed) {
+                } else if (want_t) {
                     waiting = false;
                     if ((long long)g >= limit) {
-                        state = kDone;
+                        if (P.share) exhausted = true;   // idle: may still take shared copies
+                        else state = kDone;
                     } else {
                         seq = (uint32_t)(g % (unsigned long long)P.n_seq);
                         tour = (uint32_t)(g / (unsigned long long)P.n_seq);
@@ -366,20 +407,127 @@ __global__ void __launch_bounds__(32 * 9, 1) grow_kernel(const RunDev P) {
                     cur_seq = -1;          // sequence finished: ask again next round
                 }
             }
-            if (state == kNeed && !waiting && (P.alg == PERM_ALG2 || cur_seq >= 0)) {
+            if (state == kNeed && !waiting && !xbusy && !exhausted && (P.alg == PERM_ALG2 || cur_seq >= 0)) {
                 // start a tour at the empty walk (Sec. 1: W(empty) = 1)
                 n = 0; cx = cy = cz = 0; maxn = 0; W = 1.0; ordinal = 0ull;
-                top = 0; sbase = 0;
+                top = 0; sbase = 0; bot = 0;
+                own = sidx; did = 0u; donated = false;
                 const int s0 = hash_insert<Key>(hash, ST, lane, P.log2h,
                                                 KeyCodec<D, Key>::encode(0, 0, 0));
                 if (s0 < 0) { set_status(P.status, PERM_EOVERFLOW); state = kDone; }
                 else { sites[lane] = (uint16_t)s0; state = kNode; }
             }
         }
+        if (P.share) {
+            // ---------------- shared copies: idle walks take queued ones ----------------
+            const bool idle = state == kNeed && (waiting || xbusy || exhausted);
+            const unsigned hm = __ballot_sync(kFull, idle);
+            if (hm && *(volatile int *)&head->queued > 0) {
+                const int leader = __ffs(hm) - 1;
+                unsigned long long base = 0ull, take = 0ull;
+                if (lane == leader) {
+                    for (int attempt = 0; attempt < 8; ++attempt) {
+                        const unsigned long long h0 = *(volatile unsigned long long *)P.dq_head;
+                        const unsigned long long t0 = *(volatile unsigned long long *)P.dq_tail;
+                        if (t0 <= h0) break;
+                        unsigned long long k = t0 - h0;
+                        k = k < (unsigned long long)__popc(hm) ? k : (unsigned long long)__popc(hm);
+                        if (atomicCAS(P.dq_head, h0, h0 + k) == h0) { base = h0; take = k; break; }
+                    }
+                }
+                base = __shfl_sync(kFull, base, leader);
+                take = __shfl_sync(kFull, take, leader);
+                const unsigned rk = __popc(hm & lt_mask);
+                if (idle && rk < take) {
+                    const unsigned long long pos = base + rk;
+                    const uint32_t cell = (uint32_t)pos & dq_mask;
+                    const uint32_t round = (uint32_t)(pos >> P.dq_log2cap);
+                    bool ok = false;
+                    for (int spin = 0; spin < kCellSpin; ++spin) {
+                        if (*(volatile unsigned int *)(P.dq_ready + cell) == round + 1u) { ok = true; break; }
+                        __nanosleep(32);
+                    }
+                    if (!ok || pos + 1ull >= (1ull << 32)) {
+                        set_status(P.status, ok ? PERM_EOVERFLOW : PERM_ETIMEOUT);
+                        state = kDone;
+                    } else {
+                        __threadfence();
+                        const unsigned char *cb = P.dq_cells + (size_t)cell * (size_t)P.dq_cell_bytes;
+                        const uint4 h0 = __ldcg(reinterpret_cast<const uint4 *>(cb));
+                        const uint2 h1 = __ldcg(reinterpret_cast<const uint2 *>(cb + 16));
+                        const double cw = __longlong_as_double(__ldcg(reinterpret_cast<const long long *>(cb + 24)));
+                        const int dp = (int)h0.w;
+                        const uint32_t meta = h1.x;
+                        // the walk up to the branch point, site by site (Sec. 1); the keys
+                        // come in 16-byte vectors, four vectors in flight
+                        const uint4 *kv = reinterpret_cast<const uint4 *>(cb + 32);
+                        const int nv = (dp + kKeysPerVec<Key>) / kKeysPerVec<Key>;
+                        bool ovf = false;
+                        for (int v0 = 0; v0 < nv && !ovf; v0 += 4) {
+                            KeyVec<Key> buf[4];
+#pragma unroll
+                            for (int u = 0; u < 4; ++u)
+                                buf[u].v = (v0 + u < nv) ? __ldcg(kv + v0 + u) : make_uint4(0u, 0u, 0u, 0u);
+#pragma unroll
+                            for (int u = 0; u < 4; ++u) {
+#pragma unroll
+                                for (int e = 0; e < kKeysPerVec<Key>; ++e) {
+                                    const int k = (v0 + u) * kKeysPerVec<Key> + e;
+                                    if (k <= dp && !ovf) {
+                                        const int sl = hash_insert<Key>(hash, ST, lane, P.log2h, buf[u].k[e]);
+                                        if (sl < 0) ovf = true;
+                                        else sites[(uint32_t)k * ST + lane] = (uint16_t)sl;
+                                    }
+                                }
+                            }
+                        }
+                        __threadfence();
+                        *(volatile unsigned int *)(P.dq_free + cell) = round + 1u;
+                        if (ovf) { set_status(P.status, PERM_EOVERFLOW); state = kDone; }
+                        else {
+                            own = (int)h0.x; seq = h0.y; tour = h0.z;
+                            g = (unsigned long long)tour * (unsigned long long)P.n_seq + seq;
+                            did = (uint32_t)(pos + 1ull);
+                            ordinal = (unsigned long long)did << 32;
+                            donated = false; maxn = 0;
+                            top = 0; sbase = 0; bot = 0;
+                            const int cnt = (int)((meta >> 16) & 7u);
+                            const uint32_t dirs = meta >> 19;
+                            pend_dir = (int)(dirs & 7u);
+                            pend_w = cw;
+                            pend_depth = dp;
+                            if (cnt > 1) {
+                                smeta[lane] = (uint32_t)dp | ((uint32_t)(cnt - 1) << 16) | ((dirs >> 3) << 19);
+                                sw[lane] = cw;
+                                top = 1;
+                            }
+                            un_lo = dp + 1; un_hi = dp; tour_end = false;
+                            waiting = false;
+                            state = kUnwindState;      // resumes at the branch point below
+                        }
+                    }
+                }
+            }
+            const int hcount = __popc(__ballot_sync(kFull, state == kNeed && (waiting || xbusy || exhausted)));
+            if (lane == 0 && hcount != my_hungry) {
+                atomicAdd(P.hungry, hcount - my_hungry);
+                my_hungry = hcount;
+            }
+            // walks with no tickets left stop once every tour of the launch has
+            // finished (or the run has failed)
+            if (state == kNeed && exhausted &&
+                ((long long)*(volatile unsigned long long *)&head->fin >= limit || *(volatile int *)&head->status != 0))
+                state = kDone;
+        }
         const unsigned live = __ballot_sync(kFull, state != kDone);
         if (!live) break;
         ++my_iters;
-        if (__all_sync(kFull, state == kDone || (state == kNeed && waiting))) __nanosleep(500);
+        if (__all_sync(kFull, state == kDone || (state == kNeed && (waiting || xbusy || exhausted)))) {
+            __nanosleep(idle_ns);
+            idle_ns = idle_ns < 4000u ? 2u * idle_ns : 4000u;
+        } else {
+            idle_ns = 500u;
+        }
 
         // ---------------- one node ----------------
         if (state == kNode) {
@@ -402,7 +550,7 @@ __global__ void __launch_bounds__(32 * 9, 1) grow_kernel(const RunDev P) {
                 }
                 Tp = pack_threshold(__ddiv_rn(old, (double)Mb));
             }
-            atomicAdd(&Xrow[n], W);
+            atomicAdd(P.X + (size_t)own * L + n, W);
             maxn = n > maxn ? n : maxn;
             ++my_steps;
 
@@ -437,6 +585,7 @@ __global__ void __launch_bounds__(32 * 9, 1) grow_kernel(const RunDev P) {
                 }
             }
 
+            if ((uint32_t)ordinal == 0xFFFFFFFFu) set_status(P.status, PERM_EOVERFLOW);
             ordinal += 1ull;
             if (o.outcome == kChildren) {
                 const int c = o.dec.c;
@@ -459,7 +608,7 @@ __global__ void __launch_bounds__(32 * 9, 1) grow_kernel(const RunDev P) {
                         smeta[(uint32_t)ti * ST + lane] = (uint32_t)n | ((uint32_t)(c - 1) << 16) | (rest << 19);
                         sw[(uint32_t)ti * ST + lane] = o.child_w;
                         ++top;
-                        my_max_stack = top > my_max_stack ? top : my_max_stack;
+                        my_max_stack = top - bot > my_max_stack ? top - bot : my_max_stack;
                     }
                 }
                 const int dir0 = (int)(o.dec.dirs & 7u);
@@ -471,18 +620,62 @@ __global__ void __launch_bounds__(32 * 9, 1) grow_kernel(const RunDev P) {
                     sites[(uint32_t)n * ST + lane] = (uint16_t)s0;
                 }
                 W = o.child_w;
+                if (snapshot && P.share && top - bot >= 2 && *(volatile int *)&head->want_don > 0) {
+                    // hand the oldest waiting copy record to an idle walk: its subtree
+                    // grows there, and its weights still go to this tour's row `own`
+                    const uint32_t bi = (uint32_t)(bot & (K - 1)) * ST + lane;
+                    const uint32_t bm = bot < sbase ? gmeta[bot] : smeta[bi];
+                    const double bw = bot < sbase ? gwt[bot] : sw[bi];
+                    const int bdp = (int)(bm & 0xFFFFu);
+                    if (P.n_max - bdp >= kMinShareGap && atomicSub(&head->want_don, 1) > 0) {
+                        unsigned long long pos = 0ull;
+                        bool got = false;
+                        for (int attempt = 0; attempt < 8; ++attempt) {
+                            const unsigned long long t0 = *(volatile unsigned long long *)P.dq_tail;
+                            const uint32_t c0 = (uint32_t)t0 & dq_mask;
+                            if (*(volatile unsigned int *)(P.dq_free + c0) != (uint32_t)(t0 >> P.dq_log2cap)) break;
+                            if (atomicCAS(P.dq_tail, t0, t0 + 1ull) == t0) { pos = t0; got = true; break; }
+                        }
+                        if (got) {
+                            if (did == 0u && !donated) { P.outst[sidx] = 2u; donated = true; }
+                            else atomicAdd(P.outst + own, 1u);
+                            const uint32_t cell = (uint32_t)pos & dq_mask;
+                            unsigned char *cb = P.dq_cells + (size_t)cell * (size_t)P.dq_cell_bytes;
+                            *reinterpret_cast<uint4 *>(cb) = make_uint4((uint32_t)own, seq, tour, (uint32_t)bdp);
+                            *reinterpret_cast<uint2 *>(cb + 16) = make_uint2(bm, 0u);
+                            *reinterpret_cast<double *>(cb + 24) = bw;
+                            uint4 *kv = reinterpret_cast<uint4 *>(cb + 32);
+                            const int nv = (bdp + kKeysPerVec<Key>) / kKeysPerVec<Key>;
+                            for (int v = 0; v < nv; ++v) {
+                                KeyVec<Key> buf;
+#pragma unroll
+                                for (int e = 0; e < kKeysPerVec<Key>; ++e) {
+                                    const int k = v * kKeysPerVec<Key> + e;
+                                    buf.k[e] = k <= bdp ? hash[(uint32_t)sites[(uint32_t)k * ST + lane] * ST + lane] : (Key)0;
+                                }
+                                kv[v] = buf.v;
+                            }
+                            __threadfence();
+                            *(volatile unsigned int *)(P.dq_ready + cell) = (uint32_t)(pos >> P.dq_log2cap) + 1u;
+                            bot += 1;
+                            if (sbase < bot) sbase = bot;
+                        } else {
+                            atomicAdd(&head->want_don, 1);
+                        }
+                    }
+                }
             } else {
                 // leaf: resume the most recent waiting copy, or end the tour
-                if (top == sbase && sbase > 0) {
-                    sbase -= K / 2;
-                    for (int i = 0; i < K / 2; ++i) {
-                        const int idx = sbase + i;
+                if (top == sbase && sbase > bot) {
+                    const int lo = sbase - K / 2 > bot ? sbase - K / 2 : bot;
+                    for (int idx = lo; idx < sbase; ++idx) {
                         smeta[(uint32_t)(idx & (K - 1)) * ST + lane] = gmeta[idx];
                         sw[(uint32_t)(idx & (K - 1)) * ST + lane] = gwt[idx];
                     }
+                    sbase = lo;
                 }
                 const int hi = n < P.n_max - 1 ? n : P.n_max - 1;
-                if (top == 0) {
+                if (top == bot) {
                     un_lo = 0; un_hi = hi; tour_end = true;
                 } else {
                     const int ti = (top - 1) & (K - 1);
@@ -528,16 +721,32 @@ __global__ void __launch_bounds__(32 * 9, 1) grow_kernel(const RunDev P) {
             }
         }
 
-        // ---------------- end of tour: per-tour sums into Q (whole warp) ----------------
-        unsigned fm = __ballot_sync(kFull, state == kFlush);
-        if (fm) {
+        // ---------------- end of a tour (part): per-tour sums into Q (whole warp) ----------------
+        if (__any_sync(kFull, state == kFlush)) {
+            if (state == kFlush) {
+                if (did == 0u && !donated) {
+                    // the whole tour grew on this walk
+                    frow = sidx; fmaxn = maxn; do_flush = true; shared_flush = false;
+                } else {
+                    // parts of the tour grew elsewhere: the last part to end flushes
+                    const unsigned om = atomicMax(P.tmaxn + own, (unsigned)maxn);
+                    __threadfence();
+                    const unsigned left = atomicSub(P.outst + own, 1u);
+                    do_flush = (left == 1u);
+                    shared_flush = true;
+                    frow = own;
+                    fmaxn = (int)(om > (unsigned)maxn ? om : (unsigned)maxn);
+                    if (!do_flush && did == 0u) xbusy = true;
+                }
+            }
+            unsigned fm = __ballot_sync(kFull, state == kFlush && do_flush);
             __threadfence();
             __syncwarp();
             while (fm) {
                 const int src = __ffs(fm) - 1;
                 fm &= fm - 1u;
-                const int s_slot = __shfl_sync(kFull, sidx, src);
-                const int s_maxn = __shfl_sync(kFull, maxn, src);
+                const int s_slot = __shfl_sync(kFull, frow, src);
+                const int s_maxn = __shfl_sync(kFull, fmaxn, src);
                 const int s_seq = __shfl_sync(kFull, cur_seq, src);
                 double *Xr = P.X + (size_t)s_slot * L;
                 double *Qr = (P.alg == PERM_ALG1) ? P.Qn + (size_t)(s_seq < 0 ? 0 : s_seq) * L : P.Qn;
@@ -562,15 +771,24 @@ __global__ void __launch_bounds__(32 * 9, 1) grow_kernel(const RunDev P) {
             __threadfence();
             __syncwarp();
             if (state == kFlush) {
-                if (P.alg == PERM_ALG2) atomicAdd(P.finished, 1ull);
-                if (P.alg == PERM_ALG1) {
-                    seq_t += 1;
-                    P.seq_M[cur_seq] = (unsigned long long)seq_t;
+                if (do_flush) {
+                    if (shared_flush) {
+                        P.tmaxn[frow] = 0u;
+                        __threadfence();
+                        *(volatile unsigned int *)(P.outst + frow) = kRowFree;
+                    }
+                    atomicAdd(P.finished, 1ull);
+                    if (P.alg == PERM_ALG1) {
+                        seq_t += 1;
+                        P.seq_M[cur_seq] = (unsigned long long)seq_t;
+                    }
                 }
+                own = sidx; did = 0u; donated = false; do_flush = false;
                 state = kNeed;
             }
         }
     }
+    if (P.share && lane == 0 && my_hungry != 0) atomicAdd(P.hungry, -my_hungry);
 
     // statistics, then tell the refresher this warp is done
     unsigned long long tot = my_steps, cps = my_copies;

@@ -43,6 +43,19 @@ struct RunDev {
     unsigned long long *finished;  // Alg. 2: tours finished (admission of new tours)
     long long ramp_c0;             // admission: in flight <= c0 + gamma * finished
     unsigned long long ramp_gamma_q16;
+    // shared copies (snapshot form of Alg. 2): a walk with no tour to start
+    // takes a waiting copy from the bottom of another walk's stack
+    int share;                     // 1: on
+    int dq_log2cap;                // ring of 2^dq_log2cap donation cells
+    int dq_cell_bytes;             // header (32 bytes) + keys of sites 0..n_max, multiple of 16
+    unsigned char *dq_cells;
+    unsigned long long *dq_head;   // donations taken
+    unsigned long long *dq_tail;   // donations reserved
+    unsigned int *dq_ready;        // per cell: round + 1 once written for that round
+    unsigned int *dq_free;         // per cell: first round that may write it
+    unsigned int *outst;           // per walk: live parts of its tour (kRowFree: row unused)
+    unsigned int *tmaxn;           // per walk: deepest length over the parts of its tour
+    int *hungry;                   // walks waiting for work
     int *status;
     // optional sampled trace
     perm_trace_record *trace;

@@ -15,11 +15,10 @@ import pytest
 
 import paper_2002_03000_gb300 as pg
 from oracle import oracle as orc
-from tests.gpu_util import Run, torch_cuda
+from tests.gpu_util import REL_W, SIGMA_FLOOR, Run, replay, torch_cuda, zscores
 
 pytestmark = pytest.mark.gpu
 
-REL_W = 1e-12
 
 
 def _rel_close(a, b, rel):
@@ -69,27 +68,6 @@ def test_alg1_matches_oracle(d, n_max, N, tours):
     assert np.allclose(lc_g, lc_o, rtol=0, atol=1e-10)
 
 
-# Relative-error floor for nearly deterministic lengths.  With many concurrent
-# walks and shared snapshot thresholds, the per-tour variance misses the
-# correlation that a common threshold induces between tours; it matters only
-# where the intrinsic variance is tiny (n = 2: estimated 2.9e-6 against a
-# spread of 7.6e-6 over 20 seeds of 4096 x 8 tours; at n >= 3 the two agree).
-SIGMA_FLOOR = 1e-5
-
-
-def _zs(lc, rv, exact):
-    """z-scores of the estimates against exact c_n; an estimate that is exact
-    with zero estimated variance (short lengths, where every weight is equal)
-    scores 0."""
-    ex = np.array(exact, dtype=float)
-    rel = np.exp(lc[: len(ex)] - np.log(ex)) - 1.0
-    rv = rv[: len(ex)]
-    exact_zero = (np.abs(rel) < 1e-12) & (rv == 0.0)
-    with np.errstate(divide="ignore", invalid="ignore"):
-        z = rel / np.sqrt(rv + SIGMA_FLOOR ** 2)
-    return np.where(exact_zero, 0.0, z)
-
-
 @pytest.mark.parametrize("d,n_max,N,tours", [(2, 16, 12, 20000), (3, 11, 12, 8000), (2, 16, 4096, 40)])
 def test_snapshot_counting_theorem(d, n_max, N, tours, exact_counts):
     """Snapshot thresholds keep the estimator unbiased: c_n within 4 sigma of the
@@ -105,7 +83,7 @@ def test_snapshot_counting_theorem(d, n_max, N, tours, exact_counts):
     assert S[0] == M and S[1] == M
     assert math.isclose(math.exp(lc[0]), 1.0, rel_tol=1e-12)
     assert math.isclose(math.exp(lc[1]), 2 * d, rel_tol=1e-12)
-    z = _zs(lc, rv, exact_counts[d][: n_max + 1])
+    z = zscores(lc, rv, exact_counts[d][: n_max + 1])
     assert np.all(np.isfinite(z[2:])) and np.max(np.abs(z[2:])) < 4.0, z
     # and against the oracle (independent runs): combined 4 sigma
     o = orc.Oracle(d, n_max, N, seed=2)
@@ -116,25 +94,6 @@ def test_snapshot_counting_theorem(d, n_max, N, tours, exact_counts):
     with np.errstate(divide="ignore", invalid="ignore"):
         zz = np.where((np.abs(diff) < 1e-12) & (var == 0.0), 0.0, diff / np.sqrt(var))
     assert np.all(np.abs(zz) < 4.0), zz
-
-
-def _replay(recs, coords, d, n_max, seed):
-    bad = []
-    for rec, co in zip(recs, coords):
-        n = rec.n
-        ref = orc.step(d, n_max, co[: n + 1], rec.W, rec.T, int(rec.M), int(rec.ordinal),
-                       int(rec.seq), int(rec.tour), seed)
-        ok = (rec.outcome == ref["outcome"] and rec.a_plus == ref["a_plus"] and
-              rec.free_mask == ref["free_mask"] and rec.c == ref["c"] and
-              list(rec.dirs[: rec.c]) == ref["dirs"])
-        if ref["outcome"] >= 2:
-            ok &= np.float32(rec.r).tobytes() == np.float32(ref["r"]).tobytes()
-            ok &= int(rec.survive_K) == int(ref["survive_K"])
-        if ref["outcome"] == 3:
-            ok &= abs(rec.child_w - ref["child_w"]) <= REL_W * abs(ref["child_w"])
-        if not ok:
-            bad.append((n, rec.outcome, ref))
-    return bad
 
 
 @pytest.mark.parametrize("d,n_max,N,tours,every,tour_every",
@@ -155,12 +114,12 @@ def test_full_size_sampled_nodes_replay(d, n_max, N, tours, every, tour_every, e
         M = run.tables()["M"][0]
     assert st["status"] == 0
     assert count > 200
-    bad = _replay(recs, coords, d, n_max, seed)
+    bad = replay(recs, coords, d, n_max, seed)
     assert not bad, bad[:3]
     assert M == N * tours and S[0] == M and S[1] == M
     assert math.isclose(math.exp(lc[1]), 2 * d, rel_tol=1e-12)
     ex = exact_counts[d]
-    z = _zs(lc, rv, ex[: min(len(ex), n_max + 1)])
+    z = zscores(lc, rv, ex[: min(len(ex), n_max + 1)])
     assert np.all(np.abs(z[2:]) < 4.0), z
     # every length up to n_max is reached, and the histogram is roughly flat
     assert np.all(S > 0)

@@ -1,0 +1,70 @@
+"""Copies grown on other walks ("shared copies").
+
+Sec. 2 grows the c copies of an enriched state independently of each other,
+so a waiting copy may be grown by any walk.  A walk with no tour to start
+(the admission limit early in a run, or no tickets left at its end) takes the
+oldest waiting copy of another walk's tour, rebuilds the walk up to the branch
+point and grows the copy's subtree; the weights of that part still count for
+the tour that made the copy (its per-tour sum, and the tour finishes once
+all of its parts have).  The runs here start with most walks idle, so many
+copies move: every tour still finishes exactly once, the estimates stay
+unbiased (c_n within 4 sigma of the exact counts, S_0 = S_1 = M), and sampled
+nodes of moved parts (ordinal high word = part id) replay bit for bit in the
+oracle's growth step.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from tests.gpu_util import Run, replay, torch_cuda, zscores
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.mark.parametrize("d,n_max,N,tours,every", [(2, 200, 64, 64, 7), (3, 120, 64, 64, 5)])
+def test_moved_parts_replay_and_estimates(d, n_max, N, tours, every, exact_counts):
+    torch_cuda()
+    seed = 3
+    cap = 4000
+    with Run(d, n_max, N, seed) as run:
+        run.trace_enable(every, 1, cap)
+        run.run(tours)
+        count, recs, coords = run.trace_read()
+        lc, S, rv = run.estimates()
+        st = run.stats()
+        M = run.tables()["M"][0]
+    assert st["status"] == 0
+    assert st["shared"] > 0
+    assert M == N * tours and st["tours_finished"] == M
+    assert S[0] == M and S[1] == M
+    assert math.isclose(math.exp(lc[1]), 2 * d, rel_tol=1e-12)
+    moved = sum(1 for r in recs if int(r.ordinal) >> 32)
+    assert moved > 20, (moved, len(recs))
+    bad = replay(recs, coords, d, n_max, seed)
+    assert not bad, bad[:3]
+    ex = exact_counts[d]
+    z = zscores(lc, rv, ex[: min(len(ex), n_max + 1)])
+    assert np.all(np.abs(z[2:]) < 4.0), z
+
+
+def test_sharing_off_moves_nothing():
+    torch_cuda()
+    with Run(2, 200, 64, 3, share_copies=-1) as run:
+        run.run(16)
+        st = run.stats()
+    assert st["status"] == 0 and st["shared"] == 0 and st["tours_finished"] == 64 * 16
+
+
+def test_cumulative_runs_with_sharing():
+    """Repeated launches continue the same run; every launch ends with all of
+    its tours finished and no copy left in the ring."""
+    torch_cuda()
+    with Run(2, 300, 128, 5) as run:
+        for k in range(1, 4):
+            run.run(8)
+            st = run.stats()
+            assert st["status"] == 0
+            assert st["tours_finished"] == 128 * 8 * k
+        lc, S, rv = run.estimates()
+    assert S[0] == 128 * 24 and math.isclose(math.exp(lc[1]), 4.0, rel_tol=1e-12)
