@@ -133,6 +133,78 @@ def cpu_baseline(seconds=15.0):
                       % (rounds, rounds * w["n_seq"], steps, el)}
 
 
+def batched_vs_plain(tours):
+    """The batched form against the plain per-run form, on the same runs and tours
+    (hence the same expected error): 96 independent runs with d uniform in {2, 3},
+    n_max log-uniform in [64, 2048] and sequences log-uniform in [256, 8192]
+    (PCG64 seed 1).  Batched: every run's reset and growth captured in one CUDA
+    graph, the runs' kernels concurrent on 64 streams.  Plain: each run alone on
+    the whole GPU, one after another.  Wall time with the device synchronised."""
+    import numpy as np
+    import torch
+    import paper_2002_03000_gb300 as pg
+    from paper_2002_03000_gb300 import batch as pb
+    runs = pb.mixed_runs(96, seed=1)
+    cfgs = [pb.make_config(d, n, N, 1, run_id=i, max_seconds=120.0) for i, (d, n, N) in enumerate(runs)]
+    out = {"workload": "96 independent runs: d uniform in {2,3}, n_max log-uniform in [64,2048], "
+                       "sequences log-uniform in [256,8192] (PCG64 seed 1), %d tours per sequence" % tours,
+           "tours_per_seq": tours}
+    b = pb.Batch(cfgs, [tours] * len(runs))
+    try:
+        b.run()                                   # warm-up (and first replay)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        b.run()
+        tb = time.perf_counter() - t0
+        steps_b = sum(b.stats(r)["steps"] for r in range(len(runs)))
+        rel_b = [math.sqrt(b.estimates(r)[2][runs[r][1]]) for r in range(len(runs))]
+    except Exception as e:                        # report, do not hide
+        b.close()
+        out["error"] = str(e)
+        return out
+    b.close()
+    hs = [pg.Run(d, n, N, 1, run_id=i, max_seconds=120.0) for i, (d, n, N) in enumerate(runs)]
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    steps_p, rel_p = 0, []
+    for i, h in enumerate(hs):
+        h.run(tours)
+        steps_p += h.stats()["steps"]
+        rel_p.append(math.sqrt(h.estimates()[2][runs[i][1]]))
+    tp = time.perf_counter() - t0
+    for h in hs:
+        h.close()
+    out.update({"batched_s": tb, "plain_s": tp, "speedup": tp / tb,
+                "batched_steps_per_s": steps_b / tb, "plain_steps_per_s": steps_p / tp,
+                "median_rel_se_c_nmax": {"batched": float(np.median(rel_b)), "plain": float(np.median(rel_p))},
+                "timing": "wall clock around one graph replay / the 96 plain runs, device synchronised"})
+    return out
+
+
+def served_vs_one_at_a_time():
+    """Continuous batching against serving one request at a time, on the same
+    seeded Poisson stream (150 requests at 50 per second; d uniform in {2, 3};
+    n_max log-uniform in [64, 256]; target relative error of c_{n_max} 3e-2 or
+    1e-2; 1024 sequences; 4 tours per chunk).  Smaller n_max and looser targets
+    than the full request mix keep the session within seconds."""
+    from paper_2002_03000_gb300 import serve as ps
+    out = {"workload": "150 Poisson requests at 50/s, d in {2,3}, n_max log-uniform [64,256], "
+                       "target rel. error of c_nmax in {3e-2, 1e-2}, 1024 sequences, admitted by a "
+                       "120 GB device-memory budget"}
+    for name, mr in (("continuous", 16), ("one_at_a_time", 1)):
+        reqs = ps.poisson_requests(150, 50.0, seed=1, n_max_range=(64, 256), targets=(3e-2, 1e-2), n_seq=1024)
+        for r in reqs:
+            r.chunk_tours = 4
+        srv = ps.Server(ps.GpuEngine(max_ctas=-1 if mr > 1 else 0), hbm_budget_bytes=120e9, max_resident=mr)
+        t0 = time.perf_counter()
+        done = srv.serve(reqs)
+        el = time.perf_counter() - t0
+        sm = ps.Server.summary(done, el)
+        sm.update({"max_resident": mr, "peak_resident": srv.peak_resident, "wall_s": el})
+        out[name] = sm
+    return out
+
+
 def run_reference(args):
     world, rank, _ = dist_env()
     if rank != 0:
@@ -324,6 +396,9 @@ def run_ours(args):
         "estimates": {"log_c_nmax": float(lc[w["n_max"]]), "rel_se_c_nmax": float(math.sqrt(rv[w["n_max"]])),
                       "log_c_nmax_over_nmax": float(lc[w["n_max"]] / w["n_max"])},
     }
+    if world == 1 and not args.skip_systems:
+        line["batched"] = batched_vs_plain(args.batch_tours)
+        line["served"] = served_vs_one_at_a_time()
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(args.cpu_seconds)
     print(json.dumps(line), flush=True)
@@ -343,6 +418,8 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--skip-time-to-target", action="store_true")
     ap.add_argument("--target-cap-s", type=float, default=20.0)
+    ap.add_argument("--skip-systems", action="store_true")
+    ap.add_argument("--batch-tours", type=int, default=4)
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)

@@ -71,7 +71,8 @@ typedef struct {
     int ramp_c0;       /* Algorithm 2 admission: at most ramp_c0 + ramp_gamma * (finished
                           tours) tours are in flight.  0 = default (2); < 0 = no limit */
     double ramp_gamma; /* see ramp_c0; 0 = default (1.0) */
-    int max_ctas;      /* at most this many CTAs (SMs) for the run's walks; 0 = all SMs.
+    int max_ctas;      /* at most this many CTAs (SMs) for the run's walks; 0 = all SMs;
+                          -1 = as few CTAs as hold one walk per sequence (dense packing).
                           Lets concurrent runs share the device */
     int hash_scale;    /* per-walk occupancy hash has 2^hash_scale * 2 n_max slots
                           (rounded up to a power of 2); 0..2 */
@@ -79,7 +80,10 @@ typedef struct {
                           start (admission limit, or no tickets left) takes the oldest
                           waiting copy of another walk's tour and grows its subtree; the
                           copy's weights still count for that tour (Sec. 2: the copies
-                          grow independently).  0 = on (default), -1 = off */
+                          grow independently).  k >= 1: at most k parts of one tour grow
+                          at once; 0 = on with the default cap (4); -1 = off.  Once no
+                          tour of the run has finished for 5 ms (a start-up tree too
+                          large for a few walks), the cap rises to 1024 */
 } perm_config;
 
 /* Fill cfg with defaults for (d, n_max, n_seq, seed). */

@@ -70,13 +70,6 @@ int perm_batch_create(perm_batch_handle *out, const perm_config *cfgs, const int
     b->R = R;
     b->tours.assign(tours_per_seq, tours_per_seq + R);
 
-    // share of the SMs per run, proportional to its expected work
-    std::vector<double> work(R);
-    double total = 0.0;
-    for (int r = 0; r < R; ++r) {
-        work[r] = (double)cfgs[r].n_seq * (double)tours_per_seq[r] * (double)(cfgs[r].n_max + 1);
-        total += work[r];
-    }
     int S = n_streams > 0 ? n_streams : std::min(R, 64);
     S = std::min(S, R);
     int rc = PERM_OK;
@@ -93,10 +86,9 @@ int perm_batch_create(perm_batch_handle *out, const perm_config *cfgs, const int
     }
     for (int r = 0; rc == PERM_OK && r < R; ++r) {
         perm_config c = cfgs[r];
-        if (c.max_ctas == 0 && total > 0.0) {
-            const int share = (int)std::ceil((double)sms * work[r] / total);
-            c.max_ctas = std::max(1, std::min(sms, share));
-        }
+        // pack each run's walks into as few CTAs as shared memory allows, so that
+        // the concurrent runs share the SMs
+        if (c.max_ctas == 0) c.max_ctas = -1;
         perm_handle h = nullptr;
         rc = perm_create_ex(&h, &c);
         if (rc != PERM_OK) break;

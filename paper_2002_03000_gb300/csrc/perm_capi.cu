@@ -4,6 +4,7 @@
 // walks on the device (slots per warp, warps per CTA, CTAs), device memory,
 // launches, and the estimates of Sec. 1, eq. (4) (Alg. 1: eq. (7)) computed
 // from the tables the kernels fill.
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
@@ -36,6 +37,7 @@ struct perm_run_s {
     int *status = nullptr;
     // shared copies
     bool share = false;
+    int share_cap = 0;
     int dq_log2cap = 0, dq_cell_bytes = 0;
     unsigned char *dq_cells = nullptr;
     unsigned long long *dq_head = nullptr, *dq_tail = nullptr;
@@ -78,6 +80,12 @@ void free_all(perm_handle h) {
                     h->tmaxn, h->hungry};
     for (void *p : ptrs) if (p) cudaFree(p);
 }
+
+// Parts of one tour that may grow on other walks at once (shared copies), and the
+// larger bound used once no tour of the run has finished for kStallNs.
+constexpr int kDefaultShareCap = 4;
+constexpr int kBoostShareCap = 1024;
+constexpr long long kStallNs = 5000000;
 
 int scale_exp_host(int d, int n) { return d == 2 ? (11 * n) >> 3 : (9 * n) >> 2; }
 
@@ -134,8 +142,8 @@ int perm_create_ex(perm_handle *out, const perm_config *cfg) {
     if (cfg->threshold != PERM_THRESH_SNAPSHOT && cfg->threshold != PERM_THRESH_FRESH) return PERM_EINVAL;
     if (cfg->slots < 0 || cfg->refresh_ns < 0 || !(cfg->max_seconds >= 0.0)) return PERM_EINVAL;
     if (!(cfg->ramp_gamma >= 0.0) || cfg->ramp_gamma > 1e6) return PERM_EINVAL;
-    if (cfg->max_ctas < 0 || cfg->hash_scale < 0 || cfg->hash_scale > 2) return PERM_EINVAL;
-    if (cfg->share_copies != 0 && cfg->share_copies != -1) return PERM_EINVAL;
+    if (cfg->max_ctas < -1 || cfg->hash_scale < 0 || cfg->hash_scale > 2) return PERM_EINVAL;
+    if (cfg->share_copies < -1 || cfg->share_copies > 1024) return PERM_EINVAL;
     const int lpw = cfg->lanes_per_warp;
     if (lpw != 0 && (lpw < 1 || lpw > 32)) return PERM_EINVAL;
     const bool key64 = (d == 3 && n_max > 512);
@@ -181,6 +189,21 @@ int perm_create_ex(perm_handle *out, const perm_config *cfg) {
     auto smem_for = [&](int warps, int stride) {
         return perm::cta_smem_bytes(d, key64, n_max, log2h, h->stack_cache, warps, snap, stride);
     };
+    if (cfg->max_ctas == -1) {
+        // dense packing: the fewest CTAs (of up to 8 x 32 walks) that hold one walk
+        // per sequence, so that runs sharing the device take few SMs each
+        long long per_cta = 0;
+        for (int w = 1; w <= 8; ++w)
+            for (int l = 32; l >= 1; --l)
+                if (smem_for(w, pow2_at_least(l)) <= budget) {
+                    per_cta = std::max(per_cta, (long long)w * l);
+                    break;
+                }
+        if (per_cta > 0) {
+            const long long need = ((long long)n_seq + per_cta - 1) / per_cta;
+            h->num_sms = (int)std::max(1LL, std::min((long long)h->num_sms, need));
+        }
+    }
     long long slots = cfg->slots ? cfg->slots : (long long)n_seq;
     if (slots > n_seq) slots = n_seq;
     const long long slots_wanted = slots;
@@ -239,7 +262,8 @@ int perm_create_ex(perm_handle *out, const perm_config *cfg) {
     if (rc == PERM_OK) rc = dalloc(h, &h->status, 1);
     // shared copies: a ring of cells, each one waiting copy record plus the keys of the
     // walk up to its branch point
-    h->share = cfg->share_copies == 0 && cfg->alg == PERM_ALG2 && h->thresh == perm::kSnapshot;
+    h->share = cfg->share_copies >= 0 && cfg->alg == PERM_ALG2 && h->thresh == perm::kSnapshot;
+    h->share_cap = cfg->share_copies > 0 ? cfg->share_copies : kDefaultShareCap;
     if (rc == PERM_OK && h->share) {
         int lc = 6;
         while ((1 << lc) < h->slots && lc < 12) ++lc;
@@ -301,7 +325,9 @@ static RunDev make_params(perm_handle h) {
     P.finished = h->finished;
     P.ramp_c0 = h->cfg.ramp_c0 < 0 ? -1 : (long long)h->cfg.ramp_c0;
     P.ramp_gamma_q16 = (unsigned long long)(h->cfg.ramp_gamma * 65536.0);
-    P.share = h->share ? 1 : 0;
+    P.share = h->share ? h->share_cap : 0;
+    P.share_boost = h->share ? std::max(h->share_cap, kBoostShareCap) : 0;
+    P.stall_ns = kStallNs;
     P.dq_log2cap = h->dq_log2cap; P.dq_cell_bytes = h->dq_cell_bytes; P.dq_cells = h->dq_cells;
     P.dq_head = h->dq_head; P.dq_tail = h->dq_tail; P.dq_ready = h->dq_ready; P.dq_free = h->dq_free;
     P.outst = h->outst; P.tmaxn = h->tmaxn; P.hungry = h->hungry;

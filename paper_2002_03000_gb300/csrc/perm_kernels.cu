@@ -45,7 +45,8 @@ struct CtaHead {
     int queued;              // shared copies waiting in the ring, as of the last snapshot
     int status;              // run status, as of the last snapshot
     unsigned long long fin;  // tours finished, as of the last snapshot
-    int pad[8];
+    int cap;                 // parts of one tour that may grow at once (shared copies)
+    int pad[7];
 };
 static_assert(sizeof(CtaHead) == 64, "header size");
 
@@ -212,6 +213,9 @@ __global__ void __launch_bounds__(32 * 9, 1) grow_kernel(const RunDev P) {
     // ----------------------------------------------------------------------
     if (snapshot && warp == P.worker_warps) {
         const long long t0 = global_ns();
+        unsigned long long last_fin = *(volatile unsigned long long *)P.finished;
+        long long t_change = t0;
+        if (lane == 0) *(volatile int *)&head->cap = P.share;
         for (long long it = 0;; ++it) {
             const int done = __shfl_sync(kFull, *(volatile int *)&head->done_warps, 0);
             __threadfence_block();
@@ -248,7 +252,14 @@ __global__ void __launch_bounds__(32 * 9, 1) grow_kernel(const RunDev P) {
                 *(volatile int *)&head->want_don = (int)(per < (1 << 20) ? per : (1 << 20));
                 *(volatile int *)&head->queued = (int)q;
                 *(volatile int *)&head->status = *(volatile int *)P.status;
-                *(volatile unsigned long long *)&head->fin = *(volatile unsigned long long *)P.finished;
+                const unsigned long long fin_now = *(volatile unsigned long long *)P.finished;
+                *(volatile unsigned long long *)&head->fin = fin_now;
+                // a run whose tours stop finishing is growing a start-up tree far
+                // larger than its walks can grow a few parts at a time: let its
+                // tours spread over every idle walk from then on
+                const long long now = global_ns();
+                if (fin_now != last_fin) { last_fin = fin_now; t_change = now; }
+                else if (now - t_change > P.stall_ns) *(volatile int *)&head->cap = P.share_boost;
             }
             __syncwarp();
             __nanosleep((unsigned)P.refresh_ns);
@@ -627,7 +638,12 @@ __global__ void __launch_bounds__(32 * 9, 1) grow_kernel(const RunDev P) {
                     const uint32_t bm = bot < sbase ? gmeta[bot] : smeta[bi];
                     const double bw = bot < sbase ? gwt[bot] : sw[bi];
                     const int bdp = (int)(bm & 0xFFFFu);
-                    if (P.n_max - bdp >= kMinShareGap && atomicSub(&head->want_don, 1) > 0) {
+                    // at most P.share parts of one tour grow at once (a soft cap: the
+                    // parts of a tour stay few, so each still sees its siblings' samples)
+                    bool room = true;
+                    if (!(did == 0u && !donated))
+                        room = *(volatile unsigned int *)(P.outst + own) < (unsigned)*(volatile int *)&head->cap;
+                    if (room && P.n_max - bdp >= kMinShareGap && atomicSub(&head->want_don, 1) > 0) {
                         unsigned long long pos = 0ull;
                         bool got = false;
                         for (int attempt = 0; attempt < 8; ++attempt) {

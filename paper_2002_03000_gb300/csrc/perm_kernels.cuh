@@ -45,7 +45,9 @@ struct RunDev {
     unsigned long long ramp_gamma_q16;
     // shared copies (snapshot form of Alg. 2): a walk with no tour to start
     // takes a waiting copy from the bottom of another walk's stack
-    int share;                     // 1: on
+    int share;                     // 0: off; else the most parts of one tour growing at once
+    int share_boost;               // ... once no tour of the run has finished for stall_ns
+    long long stall_ns;
     int dq_log2cap;                // ring of 2^dq_log2cap donation cells
     int dq_cell_bytes;             // header (32 bytes) + keys of sites 0..n_max, multiple of 16
     unsigned char *dq_cells;

@@ -139,7 +139,7 @@ class _Job:
 class GpuEngine:
     """Runs requests as library handles, each on its own CUDA stream."""
 
-    def __init__(self, max_ctas=38, lanes_per_warp=0):
+    def __init__(self, max_ctas=-1, lanes_per_warp=0):
         import torch
         from . import Run, _native
         self.torch, self.Run, self.nat = torch, Run, _native

@@ -68,3 +68,33 @@ def test_cumulative_runs_with_sharing():
             assert st["tours_finished"] == 128 * 8 * k
         lc, S, rv = run.estimates()
     assert S[0] == 128 * 24 and math.isclose(math.exp(lc[1]), 4.0, rel_tol=1e-12)
+
+
+@pytest.mark.parametrize("d,n_max,N,tours", [(3, 945, 2142, 4), (2, 1725, 422, 4)])
+def test_startup_trees_finish(d, n_max, N, tours):
+    """Start-up trees that one walk cannot grow in minutes (square lattice,
+    n_max 1725), and a run where unbounded spreading of parts runs away (cubic,
+    n_max 945): both finish in seconds with the default cap and its stall boost."""
+    import time
+    torch_cuda()
+    with Run(d, n_max, N, 1, max_seconds=60.0) as run:
+        t0 = time.perf_counter()
+        run.run(tours)
+        el = time.perf_counter() - t0
+        st = run.stats()
+        lc, S, rv = run.estimates()
+    assert st["status"] == 0 and st["tours_finished"] == N * tours
+    assert el < 20.0, el
+    assert S[0] == N * tours and math.isclose(math.exp(lc[1]), 2 * d, rel_tol=1e-12)
+    assert np.all(S > 0)
+
+
+def test_share_cap_argument():
+    import paper_2002_03000_gb300 as pg
+    torch_cuda()
+    with Run(2, 100, 64, 1, share_copies=2) as run:
+        run.run(8)
+        assert run.stats()["status"] == 0
+    for bad in (-2, 2000):
+        with pytest.raises(pg.PermError):
+            Run(2, 100, 64, 1, share_copies=bad)
