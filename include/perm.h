@@ -70,7 +70,7 @@ typedef struct {
                           run reports PERM_ETIMEOUT; 0 = default (600) */
     int ramp_c0;       /* Algorithm 2 admission: at most ramp_c0 + ramp_gamma * (finished
                           tours) tours are in flight.  0 = default (2); < 0 = no limit */
-    double ramp_gamma; /* see ramp_c0; 0 = default (1.0) */
+    double ramp_gamma; /* see ramp_c0; 0 = default (0.25) */
     int max_ctas;      /* at most this many CTAs (SMs) for the run's walks; 0 = all SMs;
                           -1 = as few CTAs as hold one walk per sequence (dense packing).
                           Lets concurrent runs share the device */

@@ -161,7 +161,7 @@ int perm_create_ex(perm_handle *out, const perm_config *cfg) {
     if (h->cfg.refresh_ns > 1000000) h->cfg.refresh_ns = 1000000;
     if (h->cfg.max_seconds == 0.0) h->cfg.max_seconds = 600.0;
     if (h->cfg.ramp_c0 == 0) h->cfg.ramp_c0 = 2;
-    if (h->cfg.ramp_gamma == 0.0) h->cfg.ramp_gamma = 1.0;
+    if (h->cfg.ramp_gamma == 0.0) h->cfg.ramp_gamma = 0.25;
     h->device = dev;
     h->num_sms = prop.multiProcessorCount;
     if (cfg->max_ctas > 0 && cfg->max_ctas < h->num_sms) h->num_sms = cfg->max_ctas;

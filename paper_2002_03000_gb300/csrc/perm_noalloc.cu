@@ -149,7 +149,7 @@ extern "C" int perm_run_static(const perm_config *cfg, int64_t tours_per_seq, do
     P.iterations = cnt + 5; P.finished = cnt + 6;
     P.status = reinterpret_cast<int *>(cnt + 7);
     P.ramp_c0 = cfg->ramp_c0 < 0 ? -1 : (cfg->ramp_c0 == 0 ? 2 : cfg->ramp_c0);
-    P.ramp_gamma_q16 = (unsigned long long)((cfg->ramp_gamma == 0.0 ? 1.0 : cfg->ramp_gamma) * 65536.0);
+    P.ramp_gamma_q16 = (unsigned long long)((cfg->ramp_gamma == 0.0 ? 0.25 : cfg->ramp_gamma) * 65536.0);
     P.trace = nullptr; P.trace_coords = nullptr; P.trace_count = cnt + 8;
     P.trace_cap = 0; P.trace_every = 1; P.trace_tour_every = 1;
 
