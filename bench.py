@@ -185,6 +185,37 @@ def batched_vs_plain(tours):
     return out
 
 
+def autotuned_run(tours):
+    """The autotuner's choice for the benchmark workload (walks per warp, hash size,
+    stack ring; calibrated at equal work, outside the timed region), and one complete
+    run from empty tables with it, next to one with the default layout."""
+    import torch
+    import paper_2002_03000_gb300 as pg
+    from paper_2002_03000_gb300 import batch as pb
+    w = WORKLOAD
+    cfg = pb.make_config(w["d"], w["n_max"], w["n_seq"], w["seed"], max_seconds=120.0)
+    t0 = time.perf_counter()
+    pb.autotune(cfg, probe_tours=8)
+    tune_s = time.perf_counter() - t0
+    out = {"lanes_per_warp": cfg.lanes_per_warp, "hash_scale": cfg.hash_scale, "stack_ring": cfg.stack_ring,
+           "tune_s": tune_s}
+    for name, kw in (("default", {}), ("tuned", {"lanes_per_warp": cfg.lanes_per_warp,
+                                                  "hash_scale": cfg.hash_scale, "stack_ring": cfg.stack_ring})):
+        run = pg.Run(w["d"], w["n_max"], w["n_seq"], w["seed"], max_seconds=120.0, **kw)
+        run.run(2)
+        best = None
+        for _ in range(3):
+            run.reset()
+            torch.cuda.synchronize()
+            t = time.perf_counter()
+            run.run(tours)
+            el = time.perf_counter() - t
+            best = el if best is None or el < best else best
+        out[name + "_s_per_run"] = best
+        run.close()
+    return out
+
+
 def served_vs_one_at_a_time():
     """Continuous batching against serving one request at a time, on the same
     seeded Poisson stream (150 requests at 50 per second; d uniform in {2, 3};
@@ -401,6 +432,7 @@ def run_ours(args):
                       "log_c_nmax_over_nmax": float(lc[w["n_max"]] / w["n_max"])},
     }
     if world == 1 and not args.skip_systems:
+        line["autotune"] = autotuned_run(w["tours"])
         line["batched"] = batched_vs_plain(args.batch_tours)
         line["served"] = served_vs_one_at_a_time()
     if world == 1 and not args.no_cpu_baseline:

@@ -84,6 +84,9 @@ typedef struct {
                           at once; 0 = on with the default cap (4); -1 = off.  Once no
                           tour of the run has finished for 5 ms (a start-up tree too
                           large for a few walks), the cap rises to 1024 */
+    int stack_ring;    /* waiting-copy records per walk kept in shared memory (the rest
+                          spill to global memory 8 at a time): 16, 32, 64 or 128;
+                          0 = default (16) */
 } perm_config;
 
 /* Fill cfg with defaults for (d, n_max, n_seq, seed). */
@@ -204,11 +207,14 @@ int perm_batch_estimates(perm_batch_handle b, int r, double *log_cn, double *S_n
 int perm_batch_stats(perm_batch_handle b, int r, perm_stats_t *out);
 void perm_batch_destroy(perm_batch_handle b);
 
-/* Autotuner: runs probe_tours of cfg for each walks-per-warp choice (auto, 2,
- * 4, 8, 16, 32) and hash size (hash_scale 0, 1), and writes the fastest
- * (growth steps per second) into cfg->lanes_per_warp and cfg->hash_scale.
- * Results are cached per (d, n_max, n_seq, max_ctas) for the process.
- * Synchronous; allocates and frees a handle per trial. */
+/* Autotuner (no counterpart in the paper): for each walks-per-warp choice (auto,
+ * 2, 4, 8, 16, 32), hash size (hash_scale 0, 1) and stack ring (16, 64 records),
+ * grows probe_tours tours per sequence of cfg, then times probe_tours more of
+ * the same run, and writes the fastest choice into cfg->lanes_per_warp,
+ * cfg->hash_scale and cfg->stack_ring.  Equal tours in every trial, so the
+ * comparison is at equal work.  Results are cached per (d, n_max, n_seq,
+ * max_ctas, alg, threshold) for the process.  Synchronous; allocates and frees
+ * a handle per trial.  Returns PERM_EUNSUPPORTED if no trial ran. */
 int perm_autotune(perm_config *cfg, int64_t probe_tours);
 
 /* perm_run_static -- one complete Algorithm-2 growth run that allocates

@@ -43,7 +43,8 @@ class perm_config(C.Structure):
                 ("run_id", C.c_uint32), ("alg", C.c_int), ("threshold", C.c_int),
                 ("slots", C.c_int), ("lanes_per_warp", C.c_int), ("refresh_ns", C.c_int),
                 ("max_seconds", C.c_double), ("ramp_c0", C.c_int), ("ramp_gamma", C.c_double),
-                ("max_ctas", C.c_int), ("hash_scale", C.c_int), ("share_copies", C.c_int)]
+                ("max_ctas", C.c_int), ("hash_scale", C.c_int), ("share_copies", C.c_int),
+                ("stack_ring", C.c_int)]
 
 
 class perm_stats_t(C.Structure):

@@ -69,5 +69,6 @@ def mixed_runs(count=96, seed=1, n_max_range=(64, 2048), n_seq_range=(256, 8192)
 
 
 def autotune(cfg, probe_tours=2):
-    """Pick walks per warp and hash size for cfg by short calibration runs."""
+    """Pick walks per warp, hash size and stack ring for cfg by short calibration
+    runs at equal work (written into cfg)."""
     return nat.perm_autotune(cfg, probe_tours)

@@ -153,55 +153,63 @@ int perm_batch_stats(perm_batch_handle b, int r, perm_stats_t *out) {
 void perm_batch_destroy(perm_batch_handle b) { batch_free(b); }
 
 // ---------------------------------------------------------------------------
-// Autotuner: short calibration runs over walks per warp and hash size; the
-// best configuration (growth steps per second) is written back and cached per
-// (d, n_max, n_seq, max_ctas).
+// Autotuner: short calibration runs over walks per warp, hash size and the
+// shared-memory stack ring ("spill tile").  Each trial first grows probe_tours
+// tours per sequence (start-up), then times probe_tours more of the same run,
+// so the trials compare steady-state tours per second at equal work.  The best
+// choice is written back and cached per (d, n_max, n_seq, max_ctas, alg, threshold).
 // ---------------------------------------------------------------------------
 namespace {
+struct TuneChoice { int lanes, hash_scale, ring; };
 std::mutex g_tune_mutex;
-std::map<std::tuple<int, int, int, int>, std::pair<int, int>> g_tune_cache;
+std::map<std::tuple<int, int, int, int, int, int>, TuneChoice> g_tune_cache;
 }  // namespace
 
 int perm_autotune(perm_config *cfg, int64_t probe_tours) {
     if (!cfg || probe_tours < 1) return PERM_EINVAL;
-    const auto key = std::make_tuple(cfg->d, cfg->n_max, cfg->n_seq, cfg->max_ctas);
+    const auto key = std::make_tuple(cfg->d, cfg->n_max, cfg->n_seq, cfg->max_ctas, cfg->alg, cfg->threshold);
     {
         std::lock_guard<std::mutex> lock(g_tune_mutex);
         auto it = g_tune_cache.find(key);
         if (it != g_tune_cache.end()) {
-            cfg->lanes_per_warp = it->second.first;
-            cfg->hash_scale = it->second.second;
+            cfg->lanes_per_warp = it->second.lanes;
+            cfg->hash_scale = it->second.hash_scale;
+            cfg->stack_ring = it->second.ring;
             return PERM_OK;
         }
     }
     const int lanes_c[] = {0, 2, 4, 8, 16, 32};
     const int hash_c[] = {0, 1};
-    double best = -1.0;
-    int best_l = 0, best_h = 0;
-    for (int hs : hash_c) {
-        for (int lw : lanes_c) {
-            perm_config c = *cfg;
-            c.lanes_per_warp = lw;
-            c.hash_scale = hs;
-            perm_handle h = nullptr;
-            if (perm_create_ex(&h, &c) != PERM_OK) continue;
-            perm_stats_t st;
-            const auto t0 = std::chrono::steady_clock::now();
-            const int rc = perm_run_sync(h, probe_tours);
-            const auto t1 = std::chrono::steady_clock::now();
-            if (rc == PERM_OK && perm_stats(h, &st) == PERM_OK) {
-                const double sec = std::chrono::duration<double>(t1 - t0).count();
-                const double rate = (double)st.steps / (sec > 0 ? sec : 1e-9);
-                if (rate > best) { best = rate; best_l = lw; best_h = hs; }
+    const int ring_c[] = {16, 64};
+    double best_s = -1.0;
+    TuneChoice best{0, 0, 0};
+    for (int ring : ring_c) {
+        for (int hs : hash_c) {
+            for (int lw : lanes_c) {
+                perm_config c = *cfg;
+                c.lanes_per_warp = lw;
+                c.hash_scale = hs;
+                c.stack_ring = ring;
+                perm_handle h = nullptr;
+                if (perm_create_ex(&h, &c) != PERM_OK) continue;
+                int rc = perm_run_sync(h, probe_tours);               // start-up
+                const auto t0 = std::chrono::steady_clock::now();
+                if (rc == PERM_OK) rc = perm_run_sync(h, probe_tours); // timed
+                const auto t1 = std::chrono::steady_clock::now();
+                if (rc == PERM_OK) {
+                    const double sec = std::chrono::duration<double>(t1 - t0).count();
+                    if (best_s < 0.0 || sec < best_s) { best_s = sec; best = TuneChoice{lw, hs, ring}; }
+                }
+                perm_destroy(h);
             }
-            perm_destroy(h);
         }
     }
-    if (best < 0.0) return PERM_EUNSUPPORTED;
-    cfg->lanes_per_warp = best_l;
-    cfg->hash_scale = best_h;
+    if (best_s < 0.0) return PERM_EUNSUPPORTED;
+    cfg->lanes_per_warp = best.lanes;
+    cfg->hash_scale = best.hash_scale;
+    cfg->stack_ring = best.ring;
     std::lock_guard<std::mutex> lock(g_tune_mutex);
-    g_tune_cache[key] = std::make_pair(best_l, best_h);
+    g_tune_cache[key] = best;
     return PERM_OK;
 }
 

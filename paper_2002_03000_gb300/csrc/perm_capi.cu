@@ -117,6 +117,7 @@ void perm_config_init(perm_config *cfg, int d, int n_max, int n_seq, uint64_t se
     cfg->max_ctas = 0;
     cfg->hash_scale = 0;
     cfg->share_copies = 0;
+    cfg->stack_ring = 0;
 }
 
 const char *perm_strerror(int code) {
@@ -144,6 +145,8 @@ int perm_create_ex(perm_handle *out, const perm_config *cfg) {
     if (!(cfg->ramp_gamma >= 0.0) || cfg->ramp_gamma > 1e6) return PERM_EINVAL;
     if (cfg->max_ctas < -1 || cfg->hash_scale < 0 || cfg->hash_scale > 2) return PERM_EINVAL;
     if (cfg->share_copies < -1 || cfg->share_copies > 1024) return PERM_EINVAL;
+    if (cfg->stack_ring != 0 && cfg->stack_ring != 16 && cfg->stack_ring != 32 &&
+        cfg->stack_ring != 64 && cfg->stack_ring != 128) return PERM_EINVAL;
     const int lpw = cfg->lanes_per_warp;
     if (lpw != 0 && (lpw < 1 || lpw > 32)) return PERM_EINVAL;
     const bool key64 = (d == 3 && n_max > 512);
@@ -157,6 +160,7 @@ int perm_create_ex(perm_handle *out, const perm_config *cfg) {
     perm_handle h = new (std::nothrow) perm_run_s();
     if (!h) return PERM_ENOMEM;
     h->cfg = *cfg;
+    if (cfg->stack_ring) h->stack_cache = cfg->stack_ring;
     if (h->cfg.refresh_ns == 0) h->cfg.refresh_ns = 4000;
     if (h->cfg.refresh_ns > 1000000) h->cfg.refresh_ns = 1000000;
     if (h->cfg.max_seconds == 0.0) h->cfg.max_seconds = 600.0;

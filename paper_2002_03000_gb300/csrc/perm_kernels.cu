@@ -30,6 +30,7 @@ namespace {
 constexpr int kStride = 32;        // interleave stride of the snapshot-state kernel
 constexpr int kUnwind = 8;         // hash deletions per walk per iteration
 constexpr int kPoolExtra = 4;      // extra tour tickets fetched per warp (snapshot)
+constexpr int kChunk = 8;          // stack records moved per spill or fill (ring >= 2 kChunk)
 constexpr unsigned kRowFree = 0xFFFFFFFFu;   // outst: the walk's tour-sum row is unused
 constexpr int kMinShareGap = 8;    // share a waiting copy only if it may still grow this many steps
 constexpr int kCellSpin = 1 << 20; // bounded wait for a donation cell being written
@@ -604,12 +605,14 @@ __global__ void __launch_bounds__(32 * 9, 1) grow_kernel(const RunDev P) {
                 if (c > 1) {
                     // copies 1..c-1 wait in one record (depth, count, steps, weight)
                     if (top - sbase == K) {
-                        for (int i = 0; i < K / 2; ++i) {
+                        // ring full: the oldest kChunk records go to global memory
+#pragma unroll
+                        for (int i = 0; i < kChunk; ++i) {
                             const int idx = sbase + i;
                             gmeta[idx] = smeta[(uint32_t)(idx & (K - 1)) * ST + lane];
                             gwt[idx] = sw[(uint32_t)(idx & (K - 1)) * ST + lane];
                         }
-                        sbase += K / 2;
+                        sbase += kChunk;
                     }
                     if (top >= P.n_max) {
                         set_status(P.status, PERM_EOVERFLOW);
@@ -683,10 +686,24 @@ __global__ void __launch_bounds__(32 * 9, 1) grow_kernel(const RunDev P) {
             } else {
                 // leaf: resume the most recent waiting copy, or end the tour
                 if (top == sbase && sbase > bot) {
-                    const int lo = sbase - K / 2 > bot ? sbase - K / 2 : bot;
-                    for (int idx = lo; idx < sbase; ++idx) {
-                        smeta[(uint32_t)(idx & (K - 1)) * ST + lane] = gmeta[idx];
-                        sw[(uint32_t)(idx & (K - 1)) * ST + lane] = gwt[idx];
+                    // ring empty: bring back up to kChunk records, all loads in flight
+                    // before the first store (one round trip to L2, not kChunk)
+                    const int lo = sbase - kChunk > bot ? sbase - kChunk : bot;
+                    uint32_t fmeta[kChunk];
+                    double fw[kChunk];
+#pragma unroll
+                    for (int i = 0; i < kChunk; ++i) {
+                        const int idx = lo + i;
+                        fmeta[i] = idx < sbase ? __ldcg(gmeta + idx) : 0u;
+                        fw[i] = idx < sbase ? __ldcg(gwt + idx) : 0.0;
+                    }
+#pragma unroll
+                    for (int i = 0; i < kChunk; ++i) {
+                        const int idx = lo + i;
+                        if (idx < sbase) {
+                            smeta[(uint32_t)(idx & (K - 1)) * ST + lane] = fmeta[i];
+                            sw[(uint32_t)(idx & (K - 1)) * ST + lane] = fw[i];
+                        }
                     }
                     sbase = lo;
                 }

@@ -73,8 +73,9 @@ def test_autotune_picks_a_runnable_layout():
     cfg = pb.make_config(2, 128, 512, 3, max_seconds=60.0)
     pb.autotune(cfg, probe_tours=2)
     assert cfg.lanes_per_warp in (0, 2, 4, 8, 16, 32) and cfg.hash_scale in (0, 1)
+    assert cfg.stack_ring in (16, 64)
     run = pg.Run(2, 128, 512, 3, lanes_per_warp=cfg.lanes_per_warp, hash_scale=cfg.hash_scale,
-                 max_seconds=60.0)
+                 stack_ring=cfg.stack_ring, max_seconds=60.0)
     run.run(4)
     assert run.stats()["status"] == 0
     run.close()
