@@ -195,7 +195,7 @@ def autotuned_run(tours):
     w = WORKLOAD
     cfg = pb.make_config(w["d"], w["n_max"], w["n_seq"], w["seed"], max_seconds=120.0)
     t0 = time.perf_counter()
-    pb.autotune(cfg, probe_tours=8)
+    pb.autotune(cfg, probe_tours=32)
     tune_s = time.perf_counter() - t0
     out = {"lanes_per_warp": cfg.lanes_per_warp, "hash_scale": cfg.hash_scale, "stack_ring": cfg.stack_ring,
            "tune_s": tune_s}

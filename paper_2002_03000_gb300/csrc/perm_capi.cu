@@ -218,6 +218,12 @@ int perm_create_ex(perm_handle *out, const perm_config *cfg) {
         for (int w = 1; w <= 8; ++w) {
             int l = (int)((per_cta + w - 1) / w);
             if (lpw) { if (l > lpw) continue; l = lpw < l ? lpw : l; }
+            // automatic: at most 4 walk warps of 8 walks.  A warp's walks take
+            // different paths through the step, so its iteration time grows with its
+            // walks, and past about 32 walks per SM more walks buy little and lengthen
+            // the start-up (cubic lattice, n_max 512, 8192 sequences: 4 x 8 walks per
+            // SM run in 0.57 s, 5 x 8 in 0.63 s)
+            else if (l > 8 || w > 4) continue;
             if (l > 32 || (long long)w * l < per_cta) continue;
             const int st = pow2_at_least(l);
             if (smem_for(w, st) > budget) continue;
