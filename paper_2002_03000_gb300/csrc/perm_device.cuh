@@ -232,7 +232,6 @@ struct NodeDecision {
     double Fs;       // survival: 1/K = Fs (1 + e) with Fs = y0 the FP32 reciprocal of K ...
     float e;         // ... and e = 1 - K y0 in FP32 (K has at most 24 significant bits)
     bool survive;
-    unsigned long long K;
 };
 
 // Exact float -> double widening by bit manipulation (normal floats).
@@ -270,10 +269,15 @@ __device__ __forceinline__ unsigned long long ceil_u64(float x) {
     return (m + ((1ull << sh) - 1ull)) >> sh;
 }
 
+// K = ceil(r 2^32), the integer survival threshold of a pruning decision (r < 1);
+// 0 when r >= 1.  Only test records carry it.
+__device__ __forceinline__ unsigned long long survive_K(float r) {
+    return r >= 1.0f ? 0ull : ceil_u64(ceilf(__fmul_rn(r, 4294967296.0f)));
+}
+
 __device__ __forceinline__ NodeDecision decide(int a, uint32_t freelist, float r, uint32_t w0,
                                                uint32_t w1, const double *aoc_row, int dE) {
     NodeDecision o;
-    o.K = 0ull;
     o.F = 0.0;
     o.Fs = 0.0;
     o.e = 0.0f;
@@ -291,24 +295,21 @@ __device__ __forceinline__ NodeDecision decide(int a, uint32_t freelist, float r
     o.c = enrich ? c_en : (surv ? 1 : 0);
     o.survive = !enrich && surv;
     o.F = aoc_row[a * 8 + (enrich ? c_en : 0)];
-    if (!enrich) o.K = ceil_u64(kf);
     // 1/K = y0 (1 + e) to ~2^-46: y0 the FP32 reciprocal, e its FP32 residual
     const float y0 = __frcp_rn(kf);
     o.e = __fmaf_rn(-kf, y0, 1.0f);
     o.Fs = widen(y0);
     // partial Fisher-Yates: c distinct free steps, draws by multiply-high on w1
+    // (the draws form one dependent chain, so it stops after c of them)
     uint32_t x = w1, list = freelist;
-#pragma unroll
-    for (int i = 0; i < 6; ++i) {
-        if (i < o.c) {
-            const uint32_t m = (uint32_t)(a - i);
-            const unsigned long long prod = (unsigned long long)x * m;
-            const int j = i + (int)(prod >> 32);
-            x = (uint32_t)prod;
-            const uint32_t vi = (list >> (3 * i)) & 7u, vj = (list >> (3 * j)) & 7u;
-            const uint32_t t = vi ^ vj;
-            list ^= (t << (3 * i)) | (t << (3 * j));
-        }
+    for (int i = 0; i < o.c; ++i) {
+        const uint32_t m = (uint32_t)(a - i);
+        const unsigned long long prod = (unsigned long long)x * m;
+        const int j = i + (int)(prod >> 32);
+        x = (uint32_t)prod;
+        const uint32_t vi = (list >> (3 * i)) & 7u, vj = (list >> (3 * j)) & 7u;
+        const uint32_t t = vi ^ vj;
+        list ^= (t << (3 * i)) | (t << (3 * j));
     }
     o.dirs = (o.c == 0) ? 0u : list;
     return o;

@@ -124,7 +124,7 @@ __device__ __forceinline__ NodeOut grow_node(const Key *hash, int stride, int la
                                              const double *aoc, int (&eslot)[2 * D]) {
     NodeOut o;
     o.a = 0; o.mask = 0; o.child_w = 0.0; o.overflow = false;
-    o.dec.c = 0; o.dec.dirs = 0u; o.dec.F = 0.0; o.dec.K = 0ull;
+    o.dec.c = 0; o.dec.dirs = 0u; o.dec.F = 0.0;
     // three independent chains: the node's random block, r, and the probes
     const Philox4 w = philox4x32_10((uint32_t)ordinal, (uint32_t)(ordinal >> 32), tour, seq, k0, k1);
     const float r = ratio_r(n, W, Tp, M);
@@ -583,7 +583,8 @@ __global__ void __launch_bounds__(32 * 9, 1) grow_kernel(const RunDev P) {
                     for (int i = 0; i < 6; ++i)
                         rec->dirs[i] = (i < o.dec.c) ? (int)((o.dec.dirs >> (3 * i)) & 7u) : -1;
                     rec->r = o.r; rec->seq = seq; rec->tour = tour; rec->pad2 = 0u;
-                    rec->ordinal = ordinal; rec->M = Mb; rec->survive_K = o.dec.K;
+                    rec->ordinal = ordinal; rec->M = Mb;
+                    rec->survive_K = (o.outcome == kPruned || o.outcome == kChildren) ? survive_K(o.r) : 0ull;
                     rec->W = W; rec->T = unpack_threshold(Tp); rec->child_w = o.child_w;
                     int32_t *cc = P.trace_coords + (size_t)idx * L * D;
                     for (int k = 0; k < n; ++k) {
@@ -883,7 +884,7 @@ __global__ void __launch_bounds__(32) debug_step_kernel(int n_max, int log2h, in
     for (int i = 0; i < 6; ++i) oi[4 + i] = (i < o.dec.c) ? (int)((o.dec.dirs >> (3 * i)) & 7u) : -1;
     out_r[b] = o.r;
     out_w[b] = o.child_w;
-    out_K[b] = o.dec.K;
+    out_K[b] = (o.outcome == kPruned || o.outcome == kChildren) ? survive_K(o.r) : 0ull;
 }
 
 __global__ void philox_kernel(int B, const uint32_t *ctr, uint32_t k0, uint32_t k1, uint32_t *out) {
