@@ -27,6 +27,9 @@ UNIT = "steps/s"
 WORKLOAD = dict(d=2, n_max=512, n_seq=4096, tours=256, seed=1)
 WORKLOAD_NAME = "plain massively parallel flatPERM, d=2, n_max=512, 4096 sequences x 256 tours"
 L2_FLUSH_BYTES = 512 << 20
+# c_0..c_16 of the square lattice (exact; self-avoiding walk counts)
+EXACT_C_SQUARE = [1, 4, 12, 36, 100, 284, 780, 2172, 5916, 16268, 44100, 120292, 324932,
+                  881500, 2374444, 6416596, 17245332]
 
 
 def bytes_per_step(d, f):
@@ -54,7 +57,9 @@ class ClockSampler:
     def __init__(self, index):
         self.index = index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", "bench_clocks_%d.csv" % index)
+        import tempfile
+        out_dir = os.environ.get("BENCH_CLOCKS_DIR", tempfile.gettempdir())
+        self.path = os.path.join(out_dir, "bench_clocks_%d.csv" % index)
 
     def __enter__(self):
         try:
@@ -214,6 +219,57 @@ def autotuned_run(tours):
         out[name + "_s_per_run"] = best
         run.close()
     return out
+
+
+LOG_MU_REF = {2: 0.970081147258, 3: 1.5441609707}     # literature values quoted in Sec. 5
+
+
+def growth_constants(sq_estimates):
+    """log mu_d from the eq. 15 fit (Sec. 5) to one complete run of each benchmark
+    workload: the square run just timed and one cubic run (n_max 512, 8192 x 128)."""
+    import numpy as np
+    import paper_2002_03000_gb300 as pg
+    from paper_2002_03000_gb300.analysis import fit_eq15
+    out = {}
+    lc2, rv2 = sq_estimates
+    cub = pg.Run(3, 512, 8192, 1, max_seconds=120.0)
+    cub.run(128)
+    lc3, _, rv3 = cub.estimates()
+    cub.close()
+    for d, lc, rv in ((2, lc2, rv2), (3, lc3, rv3)):
+        f = fit_eq15(lc, rv, n_min=64, n_max=len(lc) - 1)
+        g = fit_eq15(lc, rv, n_min=64, n_max=len(lc) - 1, log_mu=LOG_MU_REF[d])
+        out["d%d" % d] = {"log_mu": f["log_mu"], "log_mu_err": f["log_mu_err"], "gamma": f["gamma"],
+                          "log_mu_literature": LOG_MU_REF[d],
+                          "gamma_with_log_mu_fixed": g["gamma"], "fit_range": [64, len(lc) - 2],
+                          "workload": "d=2 n_max=512 4096x256" if d == 2 else "d=3 n_max=512 8192x128"}
+    return out
+
+
+def alg1_vs_alg2():
+    """Sec. 4's comparison on the exact-count lattice (square, n_max 16, 12
+    sequences): T_16, the mean |log c_n(exact) - log c_n(estimate)| over n = 1..16,
+    for Algorithm 1 (private tables, estimates averaged) and Algorithm 2 (one shared
+    table), at equal tours per sequence."""
+    import numpy as np
+    import paper_2002_03000_gb300 as pg
+    from paper_2002_03000_gb300.analysis import t_m
+    exact = np.log(np.array(EXACT_C_SQUARE, dtype=float))
+    rows = []
+    for tours in (1, 10, 100, 1000, 10000):
+        row = {"tours_per_seq": tours}
+        for name, alg in (("alg1", pg.PERM_ALG1), ("alg2", pg.PERM_ALG2)):
+            vals = []
+            for rep in range(4):
+                run = pg.Run(2, 16, 12, 100 + rep, alg=alg, max_seconds=60.0)
+                run.run(tours)
+                lc = run.estimates()[0]
+                run.close()
+                vals.append(t_m(lc, exact))
+            row[name] = float(np.mean(vals))
+        rows.append(row)
+    return {"workload": "square lattice, n_max 16, 12 sequences, 4 seeds per point",
+            "measure": "T_16 = mean over n=1..16 of |log c_n exact - log c_n estimate|", "rows": rows}
 
 
 def served_vs_one_at_a_time():
@@ -432,6 +488,8 @@ def run_ours(args):
                       "log_c_nmax_over_nmax": float(lc[w["n_max"]] / w["n_max"])},
     }
     if world == 1 and not args.skip_systems:
+        line["growth_constant"] = growth_constants((lc, rv))
+        line["alg1_vs_alg2"] = alg1_vs_alg2()
         line["autotune"] = autotuned_run(w["tours"])
         line["batched"] = batched_vs_plain(args.batch_tours)
         line["served"] = served_vs_one_at_a_time()

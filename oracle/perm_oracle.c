@@ -28,7 +28,7 @@
  *    by the z-score calibration of the estimates against exact c_n over many
  *    seeds.
  *
- * Readings of the paper taken here (each also listed in the design doc):
+ * Readings of the paper taken here:
  *  - The weight entering r is W(omega_k) before multiplication by
  *    a_+(omega_k); the children carry W'.a_+ (Sec. 2 with eq. 2).
  *  - M counts every tour started so far, the current one included; the own
