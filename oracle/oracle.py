@@ -23,6 +23,7 @@ def configure(L):
     L.orc_philox4x32_10.argtypes = [u32p, u32p, u32p]
     L.orc_philox4x32_10.restype = None
     L.orc_enumerate.argtypes = [C.c_int, C.c_int, C.POINTER(C.c_int64)]
+    L.orc_enumerate_r2.argtypes = [C.c_int, C.c_int, C.POINTER(C.c_int64), C.POINTER(C.c_int64)]
     L.orc_scale_exp.argtypes = [C.c_int, C.c_int]
     L.orc_ratio.argtypes = [C.c_int, C.c_double, C.c_double, C.c_int64]
     L.orc_ratio.restype = C.c_float
@@ -39,6 +40,7 @@ def configure(L):
     i64p = C.POINTER(C.c_int64)
     L.orc_tables.argtypes = [C.c_void_p, dp, dp, dp, i64p, i64p, i64p]
     L.orc_estimates.argtypes = [C.c_void_p, dp, dp, dp]
+    L.orc_observable_r2.argtypes = [C.c_void_p, dp]
     L.orc_destroy.argtypes = [C.c_void_p]
     L.orc_destroy.restype = None
     return L
@@ -69,6 +71,16 @@ def enumerate_cn(d: int, n: int) -> np.ndarray:
     if rc != 0:
         raise ValueError("orc_enumerate failed: %d" % rc)
     return out
+
+
+def enumerate_r2(d: int, n: int):
+    """(c_k, sum over walks of length k of |omega_k|^2) for k = 0..n, exact."""
+    c = np.zeros(n + 1, dtype=np.int64)
+    r2 = np.zeros(n + 1, dtype=np.int64)
+    rc = lib().orc_enumerate_r2(d, n, _p(c, C.c_int64), _p(r2, C.c_int64))
+    if rc != 0:
+        raise ValueError("orc_enumerate_r2 failed: %d" % rc)
+    return c, r2
 
 
 def scale_exp(d: int, n: int) -> int:
@@ -121,6 +133,26 @@ class Oracle:
         lib().orc_tables(self._h, _p(W, C.c_double), _p(S, C.c_double), _p(Q, C.c_double),
                          _p(M, C.c_int64), C.byref(steps), C.byref(ms))
         return dict(W=W, S=S, Q=Q, M=M, steps=steps.value, max_stack=ms.value)
+
+    def r2_table(self):
+        """Raw sum of W |omega_n|^2 per length (rows as in tables())."""
+        ntab = self.n_seq if self.alg == ORC_ALG1 else 1
+        R = np.zeros((self.n_max + 1) * ntab)
+        lib().orc_observable_r2(self._h, _p(R, C.c_double))
+        return R
+
+    def mean_r2(self):
+        """<|omega_n|^2> by the ratio estimator (Sec. 1, eq. 5): R_n / W_n (Alg. 1:
+        the average over sequences of R/M divided by that of W/M)."""
+        t = self.tables()
+        R = self.r2_table()
+        L = self.n_max + 1
+        ntab = self.n_seq if self.alg == ORC_ALG1 else 1
+        M = t["M"].astype(float)
+        num = sum(R[i * L:(i + 1) * L] / M[i] for i in range(ntab))
+        den = sum(t["W"][i * L:(i + 1) * L] / M[i] for i in range(ntab))
+        with np.errstate(divide="ignore", invalid="ignore"):
+            return num / den
 
     def estimates(self):
         L = self.n_max + 1

@@ -98,8 +98,13 @@ void orc_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t ou
 /* Exact enumeration (Sec. 1: c_n, the number of n-step self-avoiding walks). */
 /* ------------------------------------------------------------------------- */
 static void enum_rec(int d, int n, int depth, int *pos, unsigned char *occ,
-                     const long *stride, int64_t *c) {
+                     const long *stride, int64_t *c, int64_t *r2) {
     c[depth] += 1;
+    if (r2) {
+        int64_t s = 0;
+        for (int i = 0; i < d; ++i) s += (int64_t)pos[i] * pos[i];
+        r2[depth] += s;
+    }
     if (depth == n) return;
     for (int axis = 0; axis < d; ++axis) {
         for (int sgn = 1; sgn >= -1; sgn -= 2) {
@@ -108,7 +113,7 @@ static void enum_rec(int d, int n, int depth, int *pos, unsigned char *occ,
             for (int i = 0; i < d; ++i) idx += (long)(pos[i] + n + 1) * stride[i];
             if (!occ[idx]) {
                 occ[idx] = 1;
-                enum_rec(d, n, depth + 1, pos, occ, stride, c);
+                enum_rec(d, n, depth + 1, pos, occ, stride, c, r2);
                 occ[idx] = 0;
             }
             pos[axis] -= sgn;
@@ -116,7 +121,11 @@ static void enum_rec(int d, int n, int depth, int *pos, unsigned char *occ,
     }
 }
 
-int orc_enumerate(int d, int n, int64_t *c_out) {
+int orc_enumerate(int d, int n, int64_t *c_out) { return orc_enumerate_r2(d, n, c_out, NULL); }
+
+/* c_k and the sum over all walks of length k of the squared end-to-end distance
+ * |omega_k - omega_0|^2 (the observable of Sec. 1, eq. 5), k = 0..n. */
+int orc_enumerate_r2(int d, int n, int64_t *c_out, int64_t *r2_out) {
     if ((d != 2 && d != 3) || n < 0 || n > 24 || !c_out) return ORC_EINVAL;
     long side = 2L * n + 3;
     long total = 1, stride[3] = {1, 1, 1};
@@ -124,11 +133,11 @@ int orc_enumerate(int d, int n, int64_t *c_out) {
     unsigned char *occ = (unsigned char *)calloc((size_t)total, 1);
     if (!occ) return ORC_ENOMEM;
     int pos[3] = {0, 0, 0};
-    for (int k = 0; k <= n; ++k) c_out[k] = 0;
+    for (int k = 0; k <= n; ++k) { c_out[k] = 0; if (r2_out) r2_out[k] = 0; }
     long origin = 0;
     for (int i = 0; i < d; ++i) origin += (long)(n + 1) * stride[i];
     occ[origin] = 1;
-    enum_rec(d, n, 0, pos, occ, stride, c_out);
+    enum_rec(d, n, 0, pos, occ, stride, c_out, r2_out);
     free(occ);
     return ORC_OK;
 }
@@ -355,6 +364,7 @@ struct orc_state {
     uint32_t run;
     int ntab;              /* 1 (Alg. 2) or n_seq (Alg. 1) */
     double *Wn, *Qn;       /* ntab * (n_max+1) */
+    double *Rn;            /* ntab * (n_max+1): sum of W |omega_n|^2 (eq. 5 numerator) */
     int64_t *Sn;           /* ntab * (n_max+1) */
     int64_t *M;            /* ntab: tours started */
     int64_t *tours_done;   /* n_seq (Alg. 1); [0] counts tickets for Alg. 2 */
@@ -368,7 +378,7 @@ struct orc_state {
 
 void orc_destroy(orc_state *h) {
     if (!h) return;
-    free(h->Wn); free(h->Qn); free(h->Sn); free(h->M); free(h->tours_done);
+    free(h->Wn); free(h->Qn); free(h->Rn); free(h->Sn); free(h->M); free(h->tours_done);
     free(h->X); free(h->coords); free(h->stack); free(h->occ.box);
     free(h);
 }
@@ -387,6 +397,7 @@ int orc_create(orc_state **out, int d, int n_max, int n_seq, uint64_t seed,
     size_t L = (size_t)n_max + 1;
     h->Wn = (double *)calloc(L * h->ntab, sizeof(double));
     h->Qn = (double *)calloc(L * h->ntab, sizeof(double));
+    h->Rn = (double *)calloc(L * h->ntab, sizeof(double));
     h->Sn = (int64_t *)calloc(L * h->ntab, sizeof(int64_t));
     h->M = (int64_t *)calloc((size_t)h->ntab, sizeof(int64_t));
     h->tours_done = (int64_t *)calloc((size_t)n_seq, sizeof(int64_t));
@@ -394,7 +405,7 @@ int orc_create(orc_state **out, int d, int n_max, int n_seq, uint64_t seed,
     h->coords = (int32_t *)calloc(L * d, sizeof(int32_t));
     h->stack_cap = (long)n_max * (2 * d - 2) + 2 * d;
     h->stack = (stack_rec *)calloc((size_t)h->stack_cap, sizeof(stack_rec));
-    if (!h->Wn || !h->Qn || !h->Sn || !h->M || !h->tours_done || !h->X || !h->coords ||
+    if (!h->Wn || !h->Qn || !h->Rn || !h->Sn || !h->M || !h->tours_done || !h->X || !h->coords ||
         !h->stack || occ_init(&h->occ, d, n_max) != ORC_OK) {
         orc_destroy(h);
         return ORC_ENOMEM;
@@ -411,6 +422,7 @@ static int run_tour(orc_state *h, int tab, uint32_t seq, uint32_t tour, int64_t 
     const int d = h->d, n_max = h->n_max;
     double *Wn = h->Wn + (size_t)tab * (n_max + 1);
     double *Qn = h->Qn + (size_t)tab * (n_max + 1);
+    double *Rn = h->Rn + (size_t)tab * (n_max + 1);
     int64_t *Sn = h->Sn + (size_t)tab * (n_max + 1);
     int32_t *co = h->coords;
     long sp = 0;
@@ -426,6 +438,14 @@ static int run_tour(orc_state *h, int tab, uint32_t seq, uint32_t tour, int64_t 
         Wn[n] += W;
         Sn[n] += 1;
         h->X[n] += W;
+        {   /* the observable |omega_n|^2 weighted by W (Sec. 1, eq. 5) */
+            int64_t r2 = 0;
+            for (int i = 0; i < d; ++i) {
+                const int64_t x = co[(long)n * d + i];
+                r2 += x * x;
+            }
+            Rn[n] += W * (double)r2;
+        }
         h->steps += 1;
         node_out o;
         int rc = grow_node(d, n_max, n, co + (long)n * d, &h->occ, W, T, M, ordinal,
@@ -508,6 +528,14 @@ int orc_tables(const orc_state *h, double *Wn, double *Sn, double *Qn,
     if (M_out) for (int t = 0; t < h->ntab; ++t) M_out[t] = h->M[t];
     if (steps) *steps = h->steps;
     if (max_stack) *max_stack = h->max_stack;
+    return ORC_OK;
+}
+
+/* The raw table sum of W |omega_n|^2 (stored scale), rows as in orc_tables. */
+int orc_observable_r2(const orc_state *h, double *Rn) {
+    if (!h || !Rn) return ORC_EINVAL;
+    size_t L = (size_t)(h->n_max + 1) * h->ntab;
+    for (size_t i = 0; i < L; ++i) Rn[i] = h->Rn[i];
     return ORC_OK;
 }
 

@@ -37,6 +37,8 @@ void orc_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t ou
 /* Exact number c_k of self-avoiding walks of length k on Z^d, k = 0..n, by
  * depth-first enumeration.  Returns ORC_OK or ORC_EINVAL. */
 int orc_enumerate(int d, int n, int64_t *c_out);
+/* Same, and r2_out[k] = sum over those walks of the squared end-to-end distance. */
+int orc_enumerate_r2(int d, int n, int64_t *c_out, int64_t *r2_out);
 
 /* Power-of-two scale exponent E(n) of the stored weight (stored = W / 2^E(n)). */
 int orc_scale_exp(int d, int n);
@@ -72,6 +74,9 @@ int orc_tables(const orc_state *h, double *Wn, double *Sn, double *Qn,
                int64_t *M_out, int64_t *steps, int64_t *max_stack);
 /* Estimates: log c_n (natural log), S_n, relative variance of c_n. */
 int orc_estimates(const orc_state *h, double *log_cn, double *S_n, double *relvar_n);
+/* Raw table of sum W |omega_n|^2 per length (eq. 5 numerator; stored scale),
+ * rows as in orc_tables.  <R^2>_n = R_n / W_n (eq. 5). */
+int orc_observable_r2(const orc_state *h, double *Rn);
 void orc_destroy(orc_state *h);
 
 #ifdef __cplusplus

@@ -36,6 +36,10 @@ MUTATIONS = {
     "tour sum counts visits": ("h->X[n] += W;", "h->X[n] += 1.0;"),
     "root ratio not forced": ("if (n == 0) return 1.0f;", "if (n < 0) return 1.0f;"),
     "Philox round permutation": ("uint32_t y0 = hi1 ^ x1 ^ k0;", "uint32_t y0 = hi0 ^ x1 ^ k0;"),
+    "observable at the previous site": ("const int64_t x = co[(long)n * d + i];",
+                                        "const int64_t x = co[(long)(n > 0 ? n - 1 : 0) * d + i];"),
+    "observable not squared": ("r2 += x * x;", "r2 += x < 0 ? -x : x;"),
+    "observable unweighted": ("Rn[n] += W * (double)r2;", "Rn[n] += (double)r2;"),
 }
 
 
@@ -119,6 +123,13 @@ def _pins_hold(exact2):
             zs.append((math.exp(lc[10] - math.log(exact2[10])) - 1.0) / math.sqrt(rv[10]))
     sd = float(np.std(zs))
     if not (0.4 < sd < 2.5):
+        return False
+    # the observable estimator (Sec. 1, eq. 5) against the exact mean |omega_n|^2
+    c, r2 = orc.enumerate_r2(2, 10)
+    h = orc.Oracle(2, 10, 6, seed=8)
+    h.run(1500)
+    est = h.mean_r2()
+    if not np.all(np.abs(est[1:] / (r2[1:] / c[1:].astype(float)) - 1.0) < 0.03):
         return False
     return True
 
