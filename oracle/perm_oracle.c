@@ -552,11 +552,12 @@ int orc_estimates(const orc_state *h, double *log_cn, double *S_n, double *relva
             int64_t M = h->M[t];
             double Wt = h->Wn[(size_t)t * L + n], Qt = h->Qn[(size_t)t * L + n];
             s += (double)h->Sn[(size_t)t * L + n];
-            if (M < 2) { ok = 0; continue; }
-            double c = Wt / (double)M;
+            if (M < 1) { ok = 0; continue; }
+            double c = Wt / (double)M;            /* the sample average (eq. 4), any M >= 1 */
+            est += c;
+            if (M < 2) { ok = 0; continue; }      /* the variance needs two tours */
             double v = (Qt / (double)M - c * c) / (double)(M - 1);
             if (v < 0.0) v = 0.0;
-            est += c;
             var += v;
         }
         est /= (double)h->ntab;

@@ -29,7 +29,7 @@ struct perm_run_s {
     size_t smem = 0;
     int ntab = 1;
     // device buffers
-    double *Wn = nullptr, *Qn = nullptr, *X = nullptr, *gstk_w = nullptr;
+    double *Wn = nullptr, *Qn = nullptr, *X = nullptr, *gstk_w = nullptr, *Rn = nullptr;
     unsigned long long *Sn = nullptr, *tickets = nullptr, *seq_M = nullptr;
     unsigned long long *steps = nullptr, *max_stack = nullptr, *copies = nullptr, *refreshes = nullptr, *trace_count = nullptr;
     unsigned long long *iterations = nullptr, *finished = nullptr;
@@ -74,7 +74,7 @@ int dalloc(perm_handle h, T **p, size_t count) {
 }
 
 void free_all(perm_handle h) {
-    void *ptrs[] = {h->Wn, h->Qn, h->X, h->gstk_w, h->Sn, h->tickets, h->seq_M, h->steps,
+    void *ptrs[] = {h->Wn, h->Qn, h->Rn, h->X, h->gstk_w, h->Sn, h->tickets, h->seq_M, h->steps,
                     h->max_stack, h->copies, h->refreshes, h->iterations, h->finished, h->trace_count, h->gstk_meta, h->status, h->trace,
                     h->trace_coords, h->dq_cells, h->dq_head, h->dq_tail, h->dq_ready, h->dq_free, h->outst,
                     h->tmaxn, h->hungry};
@@ -118,6 +118,7 @@ void perm_config_init(perm_config *cfg, int d, int n_max, int n_seq, uint64_t se
     cfg->hash_scale = 0;
     cfg->share_copies = 0;
     cfg->stack_ring = 0;
+    cfg->observables = 0;
 }
 
 const char *perm_strerror(int code) {
@@ -145,6 +146,7 @@ int perm_create_ex(perm_handle *out, const perm_config *cfg) {
     if (!(cfg->ramp_gamma >= 0.0) || cfg->ramp_gamma > 1e6) return PERM_EINVAL;
     if (cfg->max_ctas < -1 || cfg->hash_scale < 0 || cfg->hash_scale > 2) return PERM_EINVAL;
     if (cfg->share_copies < -1 || cfg->share_copies > 1024) return PERM_EINVAL;
+    if (cfg->observables != 0 && cfg->observables != 1) return PERM_EINVAL;
     if (cfg->stack_ring != 0 && cfg->stack_ring != 16 && cfg->stack_ring != 32 &&
         cfg->stack_ring != 64 && cfg->stack_ring != 128) return PERM_EINVAL;
     const int lpw = cfg->lanes_per_warp;
@@ -257,6 +259,7 @@ int perm_create_ex(perm_handle *out, const perm_config *cfg) {
     if (rc == PERM_OK) rc = dalloc(h, &h->Wn, L * h->ntab);
     if (rc == PERM_OK) rc = dalloc(h, &h->Qn, L * h->ntab);
     if (rc == PERM_OK) rc = dalloc(h, &h->Sn, L * h->ntab);
+    if (rc == PERM_OK && cfg->observables) rc = dalloc(h, &h->Rn, L * h->ntab);
     if (rc == PERM_OK) rc = dalloc(h, &h->tickets, 1);
     if (rc == PERM_OK) rc = dalloc(h, &h->seq_M, (size_t)n_seq);
     if (rc == PERM_OK) rc = dalloc(h, &h->X, L * (size_t)h->slots);
@@ -329,7 +332,7 @@ static RunDev make_params(perm_handle h) {
     P.seq_target = h->seq_target;
     P.refresh_ns = h->cfg.refresh_ns;
     P.max_ns = (long long)(h->cfg.max_seconds * 1e9);
-    P.Wn = h->Wn; P.Sn = h->Sn; P.Qn = h->Qn; P.tickets = h->tickets; P.seq_M = h->seq_M;
+    P.Wn = h->Wn; P.Sn = h->Sn; P.Qn = h->Qn; P.Rn = h->Rn; P.tickets = h->tickets; P.seq_M = h->seq_M;
     P.X = h->X; P.gstk_meta = h->gstk_meta; P.gstk_w = h->gstk_w;
     P.steps = h->steps; P.max_stack = h->max_stack; P.copies = h->copies; P.refreshes = h->refreshes; P.iterations = h->iterations;
     P.finished = h->finished;
@@ -426,6 +429,7 @@ int perm_reset(perm_handle h) {
     cudaError_t e = cudaMemsetAsync(h->Wn, 0, cnt * sizeof(double), h->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(h->Qn, 0, cnt * sizeof(double), h->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(h->Sn, 0, cnt * sizeof(unsigned long long), h->stream);
+    if (e == cudaSuccess && h->Rn) e = cudaMemsetAsync(h->Rn, 0, cnt * sizeof(double), h->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(h->tickets, 0, sizeof(unsigned long long), h->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(h->seq_M, 0, sizeof(unsigned long long) * h->cfg.n_seq, h->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(h->steps, 0, sizeof(unsigned long long), h->stream);
@@ -468,11 +472,12 @@ int perm_estimates(perm_handle h, double *log_cn, double *S_n, double *relvar_n)
             const double w = W[t * L + n], q = Q[t * L + n];
             s += S[t * L + n];
             const int64_t m = M[t];
-            if (m < 2) { ok = false; continue; }
-            const double c = w / (double)m;
+            if (m < 1) { ok = false; continue; }
+            const double c = w / (double)m;       // the sample average (eq. 4), any M >= 1
+            est += c;
+            if (m < 2) { ok = false; continue; }  // the variance needs two tours
             double v = (q / (double)m - c * c) / (double)(m - 1);
             if (v < 0.0) v = 0.0;
-            est += c;
             var += v;
         }
         est /= (double)h->ntab;
@@ -481,6 +486,27 @@ int perm_estimates(perm_handle h, double *log_cn, double *S_n, double *relvar_n)
         if (S_n) S_n[n] = s;
         if (relvar_n) relvar_n[n] = (ok && est > 0.0) ? var / (est * est) : INFINITY;
     }
+    return PERM_OK;
+}
+
+int perm_observable_r2(perm_handle h, double *mean_r2, double *R_n) {
+    if (!h || !mean_r2 || !h->Rn) return PERM_EINVAL;
+    const size_t L = (size_t)h->cfg.n_max + 1, cnt = L * h->ntab;
+    std::vector<double> W(cnt), R(cnt);
+    std::vector<int64_t> M(h->ntab);
+    int rc = perm_tables(h, W.data(), nullptr, nullptr, M.data());
+    if (rc != PERM_OK) return rc;
+    if (copy_out(h, R.data(), h->Rn, cnt * sizeof(double)) != cudaSuccess) return PERM_EDEVICE;
+    for (size_t n = 0; n < L; ++n) {
+        double num = 0.0, den = 0.0;
+        for (int t = 0; t < h->ntab; ++t) {
+            if (M[t] < 1) continue;
+            num += R[(size_t)t * L + n] / (double)M[t];
+            den += W[(size_t)t * L + n] / (double)M[t];
+        }
+        mean_r2[n] = den > 0.0 ? num / den : NAN;
+    }
+    if (R_n) for (size_t i = 0; i < cnt; ++i) R_n[i] = R[i];
     return PERM_OK;
 }
 
