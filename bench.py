@@ -200,7 +200,7 @@ def autotuned_run(tours):
     w = WORKLOAD
     cfg = pb.make_config(w["d"], w["n_max"], w["n_seq"], w["seed"], max_seconds=120.0)
     t0 = time.perf_counter()
-    pb.autotune(cfg, probe_tours=32)
+    pb.autotune(cfg, probe_tours=64)
     tune_s = time.perf_counter() - t0
     out = {"lanes_per_warp": cfg.lanes_per_warp, "hash_scale": cfg.hash_scale, "stack_ring": cfg.stack_ring,
            "tune_s": tune_s}
@@ -266,7 +266,9 @@ def alg1_vs_alg2():
                 lc = run.estimates()[0]
                 run.close()
                 vals.append(t_m(lc, exact))
-            row[name] = float(np.mean(vals))
+            m = float(np.mean(vals))
+            row[name] = m if math.isfinite(m) else None   # a length no sequence reached
+
         rows.append(row)
     return {"workload": "square lattice, n_max 16, 12 sequences, 4 seeds per point",
             "measure": "T_16 = mean over n=1..16 of |log c_n exact - log c_n estimate|", "rows": rows}

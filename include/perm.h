@@ -87,6 +87,9 @@ typedef struct {
     int stack_ring;    /* waiting-copy records per walk kept in shared memory (the rest
                           spill to global memory 8 at a time): 16, 32, 64 or 128;
                           0 = default (16) */
+    int observables;   /* 1: also accumulate sum W |omega_n|^2 per length (the squared
+                          end-to-end distance, for the ratio estimator of Sec. 1,
+                          eq. 5; read with perm_observable_r2); 0 = off (default) */
 } perm_config;
 
 /* Fill cfg with defaults for (d, n_max, n_seq, seed). */
@@ -146,6 +149,15 @@ typedef struct {
     int64_t shared;       /* waiting copies handed to other walks, cumulative */
 } perm_stats_t;
 int perm_stats(perm_handle h, perm_stats_t *out);
+
+/* Mean squared end-to-end distance <|omega_n|^2>, n = 0..n_max, by the ratio
+ * estimator of Sec. 1, eq. 5: sum W |omega_n|^2 / sum W (Algorithm 1: the average
+ * over sequences of R/M divided by that of W/M).  mean_r2: caller-owned host
+ * array of n_max+1 (NaN where no walk reached the length).  R_n: optional
+ * (NULL allowed) host array receiving the raw sums at the stored weight scale,
+ * n_max+1 values (Algorithm 1: one row per sequence).  Synchronises with the
+ * run's stream.  PERM_EINVAL if the run was created with observables = 0. */
+int perm_observable_r2(perm_handle h, double *mean_r2, double *R_n);
 
 /* Sampled node trace (test support): every node whose DFS ordinal is a
  * multiple of `every`, in tours whose index within their sequence is a
@@ -209,10 +221,10 @@ void perm_batch_destroy(perm_batch_handle b);
 
 /* Autotuner (no counterpart in the paper): for each walks-per-warp choice (auto,
  * 2, 4, 8, 16, 32), hash size (hash_scale 0, 1) and stack ring (16, 64 records),
- * grows probe_tours tours per sequence of cfg, then times probe_tours more of
- * the same run, and writes the fastest choice into cfg->lanes_per_warp,
- * cfg->hash_scale and cfg->stack_ring.  Equal tours in every trial, so the
- * comparison is at equal work.  Results are cached per (d, n_max, n_seq,
+ * times a complete run of probe_tours tours per sequence of cfg from empty
+ * tables (twice; the faster counts), and writes the fastest choice into
+ * cfg->lanes_per_warp, cfg->hash_scale and cfg->stack_ring.  Equal tours in
+ * every trial, so the comparison is at equal work, start-up included.  Results are cached per (d, n_max, n_seq,
  * max_ctas, alg, threshold) for the process.  Synchronous; allocates and frees
  * a handle per trial.  Returns PERM_EUNSUPPORTED if no trial ran. */
 int perm_autotune(perm_config *cfg, int64_t probe_tours);

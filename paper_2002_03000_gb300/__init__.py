@@ -15,7 +15,7 @@ class Run:
     def __init__(self, d, n_max, n_seq, seed, run_id=0, alg=PERM_ALG2,
                  threshold=PERM_THRESH_SNAPSHOT, slots=0, lanes_per_warp=0, refresh_ns=0,
                  max_seconds=0.0, ramp_c0=0, ramp_gamma=0.0, max_ctas=0, hash_scale=0,
-                 share_copies=0, stack_ring=0):
+                 share_copies=0, stack_ring=0, observables=0):
         cfg = _native.perm_config_init(d, n_max, n_seq, seed)
         cfg.run_id = run_id
         cfg.alg = alg
@@ -30,6 +30,7 @@ class Run:
         cfg.hash_scale = hash_scale
         cfg.share_copies = share_copies
         cfg.stack_ring = stack_ring
+        cfg.observables = observables
         self.d, self.n_max, self.n_seq, self.alg = d, n_max, n_seq, alg
         self.h = _native.perm_create_ex(cfg)
 
@@ -47,6 +48,12 @@ class Run:
 
     def estimates(self):
         return _native.perm_estimates(self.h, self.n_max)
+
+    def mean_r2(self):
+        """<|omega_n|^2> by the ratio estimator (Sec. 1, eq. 5) and the raw sums
+        (needs observables=1 at creation)."""
+        rows = self.n_seq if self.alg == PERM_ALG1 else 1
+        return _native.perm_observable_r2(self.h, self.n_max, rows)
 
     def tables(self):
         rows = self.n_seq if self.alg == PERM_ALG1 else 1

@@ -35,6 +35,7 @@ EXPORTS = (
     "perm_trace_read", "perm_destroy", "perm_strerror", "perm_debug_step", "perm_debug_philox",
     "perm_run_static", "perm_batch_create", "perm_batch_run", "perm_batch_size",
     "perm_batch_estimates", "perm_batch_stats", "perm_batch_destroy", "perm_autotune",
+    "perm_observable_r2",
 )
 
 
@@ -44,7 +45,7 @@ class perm_config(C.Structure):
                 ("slots", C.c_int), ("lanes_per_warp", C.c_int), ("refresh_ns", C.c_int),
                 ("max_seconds", C.c_double), ("ramp_c0", C.c_int), ("ramp_gamma", C.c_double),
                 ("max_ctas", C.c_int), ("hash_scale", C.c_int), ("share_copies", C.c_int),
-                ("stack_ring", C.c_int)]
+                ("stack_ring", C.c_int), ("observables", C.c_int)]
 
 
 class perm_stats_t(C.Structure):
@@ -95,6 +96,7 @@ def load(path: str = LIB_PATH):
     L.perm_run_sync.argtypes = [vp, i64]
     L.perm_reset.argtypes = [vp]
     L.perm_estimates.argtypes = [vp, dp, dp, dp]
+    L.perm_observable_r2.argtypes = [vp, dp, dp]
     L.perm_tables.argtypes = [vp, dp, dp, dp, C.POINTER(i64)]
     L.perm_stats.argtypes = [vp, C.POINTER(perm_stats_t)]
     L.perm_trace_enable.argtypes = [vp, i64, i64, C.c_int]
@@ -177,6 +179,15 @@ def perm_estimates(h, n_max: int):
     lc, S, rv = np.empty(L), np.empty(L), np.empty(L)
     _check(load().perm_estimates(h, _dp(lc), _dp(S), _dp(rv)), "perm_estimates")
     return lc, S, rv
+
+
+def perm_observable_r2(h, n_max: int, rows: int = 1):
+    """(mean |omega_n|^2 by eq. 5, raw sums of W |omega_n|^2 per length and row)."""
+    L = n_max + 1
+    mean = np.empty(L)
+    raw = np.empty(L * rows)
+    _check(load().perm_observable_r2(h, _dp(mean), _dp(raw)), "perm_observable_r2")
+    return mean, raw
 
 
 def perm_tables(h, n_max: int, rows: int = 1):

@@ -325,6 +325,7 @@ __global__ void __launch_bounds__(32 * 9, 1) grow_kernel(const RunDev P) {
     unsigned long long my_iters = 0ull;
     double *Wrow = P.Wn;
     unsigned long long *Srow = P.Sn;
+    double *Rrow = P.Rn;
 
     const long long t_start = global_ns();
     for (long long iter = 0;; ++iter) {
@@ -409,6 +410,7 @@ __global__ void __launch_bounds__(32 * 9, 1) grow_kernel(const RunDev P) {
                         seq_t = (long long)P.seq_M[s];
                         Wrow = P.Wn + (size_t)s * L;
                         Srow = P.Sn + (size_t)s * L;
+                        if (P.Rn != nullptr) Rrow = P.Rn + (size_t)s * L;
                     }
                 }
                 if (state == kNeed && cur_seq >= 0 && seq_t < P.seq_target) {
@@ -563,6 +565,11 @@ __global__ void __launch_bounds__(32 * 9, 1) grow_kernel(const RunDev P) {
                 Tp = pack_threshold(__ddiv_rn(old, (double)Mb));
             }
             atomicAdd(P.X + (size_t)own * L + n, W);
+            if (P.Rn != nullptr) {
+                // the observable of Sec. 1, eq. 5: W |omega_n|^2 (exact integer square)
+                const long long r2 = (long long)cx * cx + (long long)cy * cy + (long long)cz * cz;
+                atomicAdd(Rrow + n, __dmul_rn(W, (double)r2));
+            }
             maxn = n > maxn ? n : maxn;
             ++my_steps;
 

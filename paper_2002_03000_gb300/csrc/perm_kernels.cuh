@@ -28,6 +28,7 @@ struct RunDev {
     double *Wn;
     unsigned long long *Sn;
     double *Qn;
+    double *Rn;                    // optional (nullptr: off): sum of W |omega_n|^2 per length
     unsigned long long *tickets;   // Alg. 2: tours started (M); Alg. 1: next sequence
     unsigned long long *seq_M;     // Alg. 1: tours done per sequence
     // per-walk scratch
