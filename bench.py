@@ -41,6 +41,37 @@ def bytes_per_step(d, f):
     return base + 32.0 * f
 
 
+KERNEL_SOURCES = ("perm_kernels.cu", "perm_kernels.cuh", "perm_device.cuh")
+
+
+def kernel_sources_sha256():
+    import hashlib
+    h = hashlib.sha256()
+    for name in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, "paper_2002_03000_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()
+
+
+def measured_traffic():
+    """DRAM bytes (read + write) of one growth-kernel launch of this workload, from
+    the ncu capture summarised in profiles/, if it was taken on the current kernel
+    sources; None otherwise (a stale count would mislead)."""
+    import re
+    path = os.path.join(ROOT, "profiles", "grow_kernel_c2_traffic.md")
+    try:
+        text = open(path).read()
+    except OSError:
+        return None, "no capture"
+    b = re.search(r"^bytes_per_launch:\s*(\d+)\s*$", text, re.M)
+    h = re.search(r"^kernel_sources_sha256:\s*([0-9a-f]{64})\s*$", text, re.M)
+    if not b or not h:
+        return None, "capture summary unreadable"
+    if h.group(1) != kernel_sources_sha256():
+        return None, "kernel changed since the capture"
+    return int(b.group(1)), "ncu capture of the current kernel (profiles/grow_kernel_c2_traffic.md)"
+
+
 def measured_peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -460,6 +491,7 @@ def run_ours(args):
     avg_kern_s = sum(kern_ms) / len(kern_ms) / 1000.0
     steps_per_launch = steps_total / args.steps
     peak, peak_kind = measured_peaks()
+    traffic, traffic_src = measured_traffic()
     achieved = B * steps_per_launch / avg_kern_s / 1e9
     clk = clocks.summary()
     if rank != 0:
@@ -480,7 +512,7 @@ def run_ours(args):
         "gpu_launches": 2 * args.steps,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": d2h},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak, "traffic": None,
+                     "frac": achieved / peak, "traffic": traffic, "traffic_source": traffic_src,
                      "peak_source": peak_kind, "bytes_per_step": B, "copies_per_step": f,
                      "kernel_ms": avg_kern_s * 1000.0},
         "clocks": clk,
@@ -515,7 +547,7 @@ def main():
     ap.add_argument("--skip-time-to-target", action="store_true")
     ap.add_argument("--target-cap-s", type=float, default=20.0)
     ap.add_argument("--skip-systems", action="store_true")
-    ap.add_argument("--batch-tours", type=int, default=4)
+    ap.add_argument("--batch-tours", type=int, default=16)
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
