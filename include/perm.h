@@ -205,7 +205,20 @@ int perm_debug_step(int d, int n_max, int B, const int32_t *coords, const int32_
  * sequence from empty tables) and captures all of their work -- table reset,
  * persistent growth kernel, tour-counter clamp -- into one CUDA graph with one
  * branch per stream (n_streams; 0 = min(R, 64)).  A run whose cfg.max_ctas is
- * 0 gets a share of the SMs proportional to n_seq * tours * (n_max + 1).
+ * 0 is packed into the fewest CTAs that hold one walk per sequence (as
+ * max_ctas = -1), so that the runs' kernels share the SMs.
+ * perm_batch_create_persistent makes the same batch grown by ONE persistent
+ * kernel on every SM instead: each CTA joins the run with the most tours left
+ * to start per CTA already on it (weighted by n_max + 1), grows at most one walk
+ * per sequence of it, and moves to another run once the run has no tours left to
+ * start; with no run left to start, CTAs help unfinished runs through their
+ * waiting copies.  Every run must be Alg. 2 with snapshot thresholds
+ * (PERM_EUNSUPPORTED otherwise); each is laid out for the whole grid (at most
+ * 4 x 8 walks per CTA), so its per-walk scratch scales with the SM count; its
+ * lanes_per_warp, slots and max_ctas are ignored.  The statistics and estimates
+ * follow the same law as a single run's (the scheduling differs, so results are
+ * not bit-identical to one).  The launch ends within the largest max_seconds
+ * of its runs; a run not finished by then reports PERM_ETIMEOUT.
  * perm_batch_run replays the graph (every run starts again from empty tables)
  * and waits; estimates and statistics are then read per run as for a single
  * handle.  The batch owns its handles, streams and graph.
@@ -213,6 +226,8 @@ int perm_debug_step(int d, int n_max, int B, const int32_t *coords, const int32_
 typedef struct perm_batch_s *perm_batch_handle;
 int perm_batch_create(perm_batch_handle *out, const perm_config *cfgs, const int64_t *tours_per_seq,
                       int R, int n_streams);
+int perm_batch_create_persistent(perm_batch_handle *out, const perm_config *cfgs,
+                                 const int64_t *tours_per_seq, int R);
 int perm_batch_run(perm_batch_handle b);
 int perm_batch_size(perm_batch_handle b);
 int perm_batch_estimates(perm_batch_handle b, int r, double *log_cn, double *S_n, double *relvar_n);

@@ -33,7 +33,7 @@ EXPORTS = (
     "perm_config_init", "perm_create", "perm_create_ex", "perm_set_stream", "perm_run", "perm_reset",
     "perm_run_sync", "perm_estimates", "perm_tables", "perm_stats", "perm_trace_enable",
     "perm_trace_read", "perm_destroy", "perm_strerror", "perm_debug_step", "perm_debug_philox",
-    "perm_run_static", "perm_batch_create", "perm_batch_run", "perm_batch_size",
+    "perm_run_static", "perm_batch_create", "perm_batch_create_persistent", "perm_batch_run", "perm_batch_size",
     "perm_batch_estimates", "perm_batch_stats", "perm_batch_destroy", "perm_autotune",
     "perm_observable_r2",
 )
@@ -110,6 +110,7 @@ def load(path: str = LIB_PATH):
     L.perm_debug_philox.argtypes = [C.c_int, vp, C.POINTER(u32), vp]
     L.perm_run_static.argtypes = [C.POINTER(perm_config), i64, vp, vp, vp, C.POINTER(i64), vp]
     L.perm_batch_create.argtypes = [hp, C.POINTER(perm_config), C.POINTER(i64), C.c_int, C.c_int]
+    L.perm_batch_create_persistent.argtypes = [hp, C.POINTER(perm_config), C.POINTER(i64), C.c_int]
     L.perm_batch_run.argtypes = [vp]
     L.perm_batch_size.argtypes = [vp]
     L.perm_batch_estimates.argtypes = [vp, C.c_int, dp, dp, dp]
@@ -249,6 +250,16 @@ def perm_batch_create(cfgs, tours, n_streams=0):
     t = (C.c_int64 * R)(*[int(x) for x in tours])
     b = C.c_void_p()
     _check(load().perm_batch_create(C.byref(b), arr, t, R, n_streams), "perm_batch_create")
+    return b
+
+
+def perm_batch_create_persistent(cfgs, tours):
+    """The same batch grown by one persistent launch (Alg. 2, snapshot runs only)."""
+    R = len(cfgs)
+    arr = (perm_config * R)(*cfgs)
+    t = (C.c_int64 * R)(*[int(x) for x in tours])
+    b = C.c_void_p()
+    _check(load().perm_batch_create_persistent(C.byref(b), arr, t, R), "perm_batch_create_persistent")
     return b
 
 

@@ -1,4 +1,5 @@
-"""Batched flatPERM runs: many independent runs grown by one CUDA-graph launch.
+"""Batched flatPERM runs: many independent runs grown by one CUDA-graph launch
+(per-run kernels on streams, or one persistent kernel for all runs).
 
 Thin wrapper of perm_batch_* (include/perm.h); the runs' growth happens in the
 persistent CUDA kernel, the graph is captured and replayed by the library.
@@ -13,12 +14,20 @@ from . import _native as nat
 
 
 class Batch:
-    """R independent runs; run() replays the captured graph (fresh tables)."""
+    """R independent runs; run() replays the captured graph (fresh tables).
 
-    def __init__(self, configs, tours, n_streams=0):
+    persistent=False: one growth kernel per run on up to 64 streams;
+    persistent=True: one persistent kernel on every SM grows all runs (CTAs move
+    between runs as their tours run out)."""
+
+    def __init__(self, configs, tours, n_streams=0, persistent=False):
         self.configs = list(configs)
         self.tours = [int(t) for t in tours]
-        self.b = nat.perm_batch_create(self.configs, self.tours, n_streams)
+        self.persistent = bool(persistent)
+        if self.persistent:
+            self.b = nat.perm_batch_create_persistent(self.configs, self.tours)
+        else:
+            self.b = nat.perm_batch_create(self.configs, self.tours, n_streams)
 
     def run(self):
         nat.perm_batch_run(self.b)

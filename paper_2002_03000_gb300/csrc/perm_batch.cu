@@ -1,13 +1,17 @@
 // perm_batch.cu -- many independent flatPERM runs grown by one CUDA-graph launch,
 // and the autotuner that picks each run's layout.
 //
-// A batch holds R runs (each a perm_handle with its own tables and stream).
-// Their work -- reset of the tables, the persistent growth kernel, the tour
-// counter clamp -- is captured once into a CUDA graph with one branch per
-// stream.  Replaying the graph grows every run again from empty tables; the
-// branches run concurrently, each run's kernel limited to a share of the SMs
-// proportional to its expected work (sequences x tours x (n_max + 1)), so that
-// small runs fill the device together instead of one after another.
+// A batch holds R runs (each a perm_handle with its own tables).  Their work --
+// reset of the tables, growth, the tour counter clamp -- is captured once into a
+// CUDA graph; replaying the graph grows every run again from empty tables.  Two
+// forms:
+//  * streams: one persistent growth kernel per run, on up to 64 streams, each
+//    packed into the fewest CTAs that hold its walks, so that small runs fill
+//    the device together instead of one after another;
+//  * persistent: ONE persistent kernel on every SM grows all runs; each CTA
+//    joins the run with the most tours left to start per CTA on it and moves
+//    on when that run has no tours left to start (runs whose tours all started
+//    are helped through their waiting copies once no run is open).
 #include <algorithm>
 #include <chrono>
 #include <cmath>
@@ -33,6 +37,9 @@ struct perm_batch_s {
     cudaEvent_t fork = nullptr;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
+    // persistent form
+    perm::RunDev *d_runs = nullptr;
+    int *d_ctl = nullptr;
 };
 
 namespace {
@@ -47,6 +54,8 @@ void batch_free(perm_batch_handle b) {
     if (b->fork) cudaEventDestroy(b->fork);
     for (cudaStream_t s : b->streams) cudaStreamDestroy(s);
     if (b->origin) cudaStreamDestroy(b->origin);
+    if (b->d_runs) cudaFree(b->d_runs);
+    if (b->d_ctl) cudaFree(b->d_ctl);
     delete b;
 }
 
@@ -121,6 +130,87 @@ int perm_batch_create(perm_batch_handle *out, const perm_config *cfgs, const int
         batch_free(b);
         return rc;
     }
+    *out = b;
+    return PERM_OK;
+}
+
+int perm_batch_create_persistent(perm_batch_handle *out, const perm_config *cfgs,
+                                 const int64_t *tours_per_seq, int R) {
+    if (!out || !cfgs || !tours_per_seq || R < 1) return PERM_EINVAL;
+    *out = nullptr;
+    for (int r = 0; r < R; ++r) {
+        if (tours_per_seq[r] < 0) return PERM_EINVAL;
+        if (cfgs[r].alg != PERM_ALG2 || cfgs[r].threshold != PERM_THRESH_SNAPSHOT) return PERM_EUNSUPPORTED;
+    }
+    size_t budget = 0;
+    if (perm::set_smem_limits() != cudaSuccess || perm::batch_smem_budget(&budget) != cudaSuccess)
+        return PERM_EDEVICE;
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+        return PERM_EDEVICE;
+    perm_batch_handle b = new (std::nothrow) perm_batch_s();
+    if (!b) return PERM_ENOMEM;
+    b->R = R;
+    b->tours.assign(tours_per_seq, tours_per_seq + R);
+    int rc = PERM_OK;
+    if (cudaStreamCreateWithFlags(&b->origin, cudaStreamNonBlocking) != cudaSuccess) rc = PERM_EDEVICE;
+    // one CTA per SM: every run is laid out so that any CTA of the grid may join it
+    const int grid = sms;
+    std::vector<perm::RunDev> P(R);
+    size_t smem = 0;
+    int warps = 1;
+    double max_s = 0.0;
+    for (int r = 0; rc == PERM_OK && r < R; ++r) {
+        perm_handle h = nullptr;
+        rc = perm::member_create(&h, &cfgs[r], grid, budget);
+        if (rc != PERM_OK) break;
+        b->runs.push_back(h);
+        rc = perm_set_stream(h, (void *)b->origin);
+        size_t sm = 0;
+        int w = 0;
+        if (rc == PERM_OK) rc = perm::member_params(h, b->tours[r], r, &P[r], &sm, &w);
+        smem = std::max(smem, sm);
+        warps = std::max(warps, w);
+        max_s = std::max(max_s, (double)P[r].max_ns * 1e-9);
+    }
+    const int threads = 32 * (warps + 1);
+    int ctas = 0;
+    if (rc == PERM_OK && perm::batch_grid(threads, smem, &ctas) != cudaSuccess) rc = PERM_EUNSUPPORTED;
+    if (rc == PERM_OK && cudaMalloc((void **)&b->d_runs, sizeof(perm::RunDev) * R) != cudaSuccess) rc = PERM_ENOMEM;
+    if (rc == PERM_OK && cudaMalloc((void **)&b->d_ctl, sizeof(int) * (3 * (size_t)R + 1)) != cudaSuccess) rc = PERM_ENOMEM;
+    if (rc == PERM_OK &&
+        cudaMemcpy(b->d_runs, P.data(), sizeof(perm::RunDev) * R, cudaMemcpyHostToDevice) != cudaSuccess)
+        rc = PERM_EDEVICE;
+    perm::BatchDev B;
+    B.runs = b->d_runs;
+    B.R = R;
+    B.active = b->d_ctl;
+    B.granted = b->d_ctl + R;
+    B.closed = b->d_ctl + 2 * R;
+    B.runs_open = b->d_ctl + 3 * R;
+    B.max_ns = (long long)(max_s * 1e9);
+    // capture: reset every run, the batch kernel, clamp each run's tour counter
+    if (rc == PERM_OK && cudaStreamBeginCapture(b->origin, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
+        rc = PERM_EDEVICE;
+    if (rc == PERM_OK) {
+        for (int r = 0; rc == PERM_OK && r < R; ++r) rc = perm::member_reset(b->runs[r]);
+        if (rc == PERM_OK && perm::launch_batch(B, grid, threads, smem, b->origin) != cudaSuccess) rc = PERM_EDEVICE;
+        for (int r = 0; rc == PERM_OK && r < R; ++r)
+            if (perm::launch_finalize(P[r].tickets, P[r].tour_limit, b->origin) != cudaSuccess) rc = PERM_EDEVICE;
+        cudaGraph_t g = nullptr;
+        const cudaError_t ec = cudaStreamEndCapture(b->origin, &g);
+        if (rc == PERM_OK && ec != cudaSuccess) rc = PERM_EDEVICE;
+        b->graph = g;
+        if (rc == PERM_OK && cudaGraphInstantiate(&b->exec, b->graph, 0) != cudaSuccess) rc = PERM_EDEVICE;
+    }
+    // the resets above cleared the host-side tour counts; set them again
+    for (int r = 0; rc == PERM_OK && r < R; ++r) rc = perm::member_params(b->runs[r], b->tours[r], r, &P[r], nullptr, nullptr);
+    if (rc != PERM_OK) {
+        batch_free(b);
+        return rc;
+    }
+    (void)ctas;
     *out = b;
     return PERM_OK;
 }

@@ -135,7 +135,18 @@ const char *perm_strerror(int code) {
     }
 }
 
-int perm_create_ex(perm_handle *out, const perm_config *cfg) {
+}  // extern "C"
+
+namespace {
+
+// A layout forced by a batch launch: `ctas` CTAs (the batch grid) within
+// smem_budget bytes of shared memory each.
+struct ForcedLayout {
+    int ctas;
+    size_t smem_budget;
+};
+
+int create_impl(perm_handle *out, const perm_config *cfg, const ForcedLayout *force) {
     if (!out || !cfg) return PERM_EINVAL;
     *out = nullptr;
     const int d = cfg->d, n_max = cfg->n_max, n_seq = cfg->n_seq;
@@ -190,12 +201,12 @@ int perm_create_ex(perm_handle *out, const perm_config *cfg) {
     // grows one walk; the walks of an SM are spread over about four warps so
     // that every scheduler has a walk's dependent chain to issue from.
     const bool snap = (h->thresh == perm::kSnapshot);
-    const size_t budget = prop.sharedMemPerBlockOptin;
+    const size_t budget = force ? force->smem_budget : prop.sharedMemPerBlockOptin;
     auto pow2_at_least = [](int v) { int p = 1; while (p < v) p <<= 1; return p; };
     auto smem_for = [&](int warps, int stride) {
         return perm::cta_smem_bytes(d, key64, n_max, log2h, h->stack_cache, warps, snap, stride);
     };
-    if (cfg->max_ctas == -1) {
+    if (!force && cfg->max_ctas == -1) {
         // dense packing: the fewest CTAs (of up to 8 x 32 walks) that hold one walk
         // per sequence, so that runs sharing the device take few SMs each
         long long per_cta = 0;
@@ -214,7 +225,17 @@ int perm_create_ex(perm_handle *out, const perm_config *cfg) {
     if (slots > n_seq) slots = n_seq;
     const long long slots_wanted = slots;
     int warps = 0, lanes = 0, stride = 0;
-    for (;;) {
+    if (force) {
+        // every CTA of the batch grid may join this run: the most walks up to
+        // 4 warps x 8 (the automatic layout's bound) that fit the shared memory
+        for (int w = 4; w >= 1 && !warps; --w)
+            for (int l = 8; l >= 1; --l)
+                if (smem_for(w, pow2_at_least(l)) <= budget) { warps = w; lanes = l; stride = pow2_at_least(l); break; }
+        slots = (long long)force->ctas * warps * lanes;
+        if (!warps || slots > (1LL << 30)) { cudaStreamDestroy(h->stream); delete h; return PERM_EUNSUPPORTED; }
+        h->num_sms = force->ctas;
+    }
+    for (; !force;) {
         const long long per_cta = (slots + h->num_sms - 1) / h->num_sms;
         int best_w = 0, best_l = 0, best_s = 0;
         for (int w = 1; w <= 8; ++w) {
@@ -242,7 +263,7 @@ int perm_create_ex(perm_handle *out, const perm_config *cfg) {
     if (!warps) { cudaStreamDestroy(h->stream); delete h; return PERM_EUNSUPPORTED; }
     const long long per_cta_eff = (long long)warps * lanes;
     // with the layout fixed, use every SM (sequences beyond it wait at tour boundaries)
-    if (slots < slots_wanted) {
+    if (!force && slots < slots_wanted) {
         const long long cap = (long long)h->num_sms * per_cta_eff;
         slots = slots_wanted < cap ? slots_wanted : cap;
     }
@@ -303,6 +324,12 @@ int perm_create_ex(perm_handle *out, const perm_config *cfg) {
     *out = h;
     return PERM_OK;
 }
+
+}  // namespace
+
+extern "C" {
+
+int perm_create_ex(perm_handle *out, const perm_config *cfg) { return create_impl(out, cfg, nullptr); }
 
 int perm_create(perm_handle *out, int d, int n_max, int n_seq, uint64_t seed) {
     perm_config cfg;
@@ -606,3 +633,32 @@ int perm_debug_philox(int B, const uint32_t *ctr, const uint32_t *key, uint32_t 
 }
 
 }  // extern "C"
+
+namespace perm {
+
+int member_create(perm_handle *out, const perm_config *cfg, int ctas, size_t smem_budget) {
+    if (!cfg || ctas < 1) return PERM_EINVAL;
+    if (cfg->alg != PERM_ALG2 || cfg->threshold != PERM_THRESH_SNAPSHOT) return PERM_EUNSUPPORTED;
+    const ForcedLayout f{ctas, smem_budget};
+    return create_impl(out, cfg, &f);
+}
+
+int member_params(perm_handle h, int64_t tours_per_seq, int run_index, RunDev *P, size_t *smem,
+                  int *worker_warps) {
+    if (!h || !P || tours_per_seq < 0) return PERM_EINVAL;
+    h->tour_limit = tours_per_seq * (long long)h->cfg.n_seq;
+    *P = make_params(h);
+    P->run_index = run_index;
+    if (smem) *smem = h->smem;
+    if (worker_warps) *worker_warps = h->worker_warps;
+    return PERM_OK;
+}
+
+int member_reset(perm_handle h) {
+    int rc = perm_reset(h);
+    if (rc != PERM_OK) return rc;
+    const size_t L = (size_t)h->cfg.n_max + 1;
+    return to_code(cudaMemsetAsync(h->X, 0, L * (size_t)h->slots * sizeof(double), h->stream));
+}
+
+}  // namespace perm

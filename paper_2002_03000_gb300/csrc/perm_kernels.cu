@@ -47,7 +47,9 @@ struct CtaHead {
     int status;              // run status, as of the last snapshot
     unsigned long long fin;  // tours finished, as of the last snapshot
     int cap;                 // parts of one tour that may grow at once (shared copies)
-    int pad[7];
+    int may_leave;           // batch launch: another run still has tours to start
+    int stalled;             // no tour of the run has finished for stall_ns
+    int pad[5];
 };
 static_assert(sizeof(CtaHead) == 64, "header size");
 
@@ -170,9 +172,27 @@ __device__ __forceinline__ int select_slot(const int (&eslot)[2 * D], int dir) {
 // ---------------------------------------------------------------------------
 // The persistent growth kernel.
 // ---------------------------------------------------------------------------
+// What lets a CTA leave a run before every tour of the run has finished: in a
+// batch launch, another run still has walks to grant and tours to start
+// (runs_open > 0).  The first walk to find a run's tickets exhausted marks it
+// closed (bit 0 of its flag; bit 1: all its walks granted); the first mark takes
+// the run off runs_open.  Bit 2 of the flag says that no tour of the run has
+// finished for a while (its CTAs' refreshers set and clear it): such a run
+// draws helper CTAs before other unfinished runs do.
+struct BatchLeave {
+    int *runs_open;
+    int *closed;
+    const int *ctas_on_run;   // CTAs growing this run now
+    bool helper;              // this CTA's walks take waiting copies only
+};
+constexpr int kStalledBit = 4;
+
+// The growth of one run by one CTA (Secs. 1-3): the refresher warp and the walk
+// warps.  A single-run launch calls it once (bl == nullptr: the CTA stays until
+// the run is complete); a batch launch calls it for each run a CTA joins.
 template <int D, typename Key, int MODE>
-__global__ void __launch_bounds__(32 * 9, 1) grow_kernel(const RunDev P) {
-    extern __shared__ __align__(16) unsigned char smem[];
+__device__ __forceinline__ void grow_run(const RunDev &P, unsigned char *smem, const BatchLeave *bl,
+                                         int cta_walks) {
     const int L = P.n_max + 1;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const bool snapshot = (MODE == kSnapshot);
@@ -249,10 +269,13 @@ __global__ void __launch_bounds__(32 * 9, 1) grow_kernel(const RunDev P) {
                                           *(volatile unsigned long long *)P.dq_head);
                 q = q < 0 ? 0 : (q > (1 << 30) ? (1 << 30) : q);
                 const long long want = hg - q;
-                const long long per = want > 0 ? (want + gridDim.x - 1) / gridDim.x : 0;
+                const long long nct = bl != nullptr ? (long long)max(1, *(volatile const int *)bl->ctas_on_run)
+                                                    : (long long)gridDim.x;
+                const long long per = want > 0 ? (want + nct - 1) / nct : 0;
                 *(volatile int *)&head->want_don = (int)(per < (1 << 20) ? per : (1 << 20));
                 *(volatile int *)&head->queued = (int)q;
                 *(volatile int *)&head->status = *(volatile int *)P.status;
+                *(volatile int *)&head->may_leave = (bl != nullptr && *(volatile int *)bl->runs_open > 0) ? 1 : 0;
                 const unsigned long long fin_now = *(volatile unsigned long long *)P.finished;
                 *(volatile unsigned long long *)&head->fin = fin_now;
                 // a run whose tours stop finishing is growing a start-up tree far
@@ -261,6 +284,14 @@ __global__ void __launch_bounds__(32 * 9, 1) grow_kernel(const RunDev P) {
                 const long long now = global_ns();
                 if (fin_now != last_fin) { last_fin = fin_now; t_change = now; }
                 else if (now - t_change > P.stall_ns) *(volatile int *)&head->cap = P.share_boost;
+                const int st_now = (now - t_change > P.stall_ns) ? 1 : 0;
+                if (st_now != *(volatile int *)&head->stalled) {
+                    *(volatile int *)&head->stalled = st_now;
+                    if (bl != nullptr) {
+                        if (st_now) atomicOr(bl->closed + P.run_index, kStalledBit);
+                        else atomicAnd(bl->closed + P.run_index, ~kStalledBit);
+                    }
+                }
             }
             __syncwarp();
             __nanosleep((unsigned)P.refresh_ns);
@@ -270,8 +301,7 @@ __global__ void __launch_bounds__(32 * 9, 1) grow_kernel(const RunDev P) {
                 break;
             }
         }
-        return;
-    }
+    } else if (warp < P.worker_warps) {
 
     // ----------------------------------------------------------------------
     // worker warps
@@ -287,7 +317,7 @@ __global__ void __launch_bounds__(32 * 9, 1) grow_kernel(const RunDev P) {
 
     const int gwarp = blockIdx.x * P.worker_warps + warp;
     const int slot = gwarp * P.S + lane;
-    const bool active = lane < P.S && slot < P.slots;
+    const bool active = lane < P.S && slot < P.slots && warp * P.S + lane < cta_walks;
     const int sidx = active ? slot : 0;
     uint32_t *gmeta = P.gstk_meta + (size_t)sidx * P.n_max;
     double *gwt = P.gstk_w + (size_t)sidx * P.n_max;
@@ -316,7 +346,7 @@ __global__ void __launch_bounds__(32 * 9, 1) grow_kernel(const RunDev P) {
     uint32_t did = 0u;
     bool donated = false;      // a part of this walk's own tour went to another walk
     bool xbusy = false;        // this walk's tour-sum row is still used by such a part
-    bool exhausted = false;    // no tour tickets left in this launch
+    bool exhausted = bl != nullptr && bl->helper;   // no tour tickets left (a helper takes none)
     int my_hungry = 0;         // lane 0: this warp's share of P.hungry
     unsigned idle_ns = 500u;   // back-off of a warp with nothing to grow
     int frow = 0, fmaxn = 0;   // tour-sum row to flush at a part's end, and its depth
@@ -334,6 +364,8 @@ __global__ void __launch_bounds__(32 * 9, 1) grow_kernel(const RunDev P) {
             if (lane == 0) set_status(P.status, PERM_ETIMEOUT);
             break;
         }
+        // in a batch launch a failed run stops at once, so that its CTAs move on
+        if (bl != nullptr && (iter & 255) == 0 && *(volatile int *)P.status != 0) break;
         // ---------------- tour tickets ----------------
         if (state == kNeed && xbusy && *(volatile unsigned int *)(P.outst + sidx) == kRowFree) xbusy = false;
         const bool want_t = state == kNeed && !xbusy && !exhausted;
@@ -394,6 +426,8 @@ __global__ void __launch_bounds__(32 * 9, 1) grow_kernel(const RunDev P) {
                     if ((long long)g >= limit) {
                         if (P.share) exhausted = true;   // idle: may still take shared copies
                         else state = kDone;
+                        if (bl != nullptr && atomicOr(bl->closed + P.run_index, 1) == 0)
+                            atomicSub(bl->runs_open, 1);
                     } else {
                         seq = (uint32_t)(g % (unsigned long long)P.n_seq);
                         tour = (uint32_t)(g / (unsigned long long)P.n_seq);
@@ -530,7 +564,8 @@ __global__ void __launch_bounds__(32 * 9, 1) grow_kernel(const RunDev P) {
             // walks with no tickets left stop once every tour of the launch has
             // finished (or the run has failed)
             if (state == kNeed && exhausted &&
-                ((long long)*(volatile unsigned long long *)&head->fin >= limit || *(volatile int *)&head->status != 0))
+                ((long long)*(volatile unsigned long long *)&head->fin >= limit || *(volatile int *)&head->status != 0 ||
+                 (!xbusy && *(volatile int *)&head->may_leave != 0)))
                 state = kDone;
         }
         const unsigned live = __ballot_sync(kFull, state != kDone);
@@ -849,6 +884,149 @@ __global__ void __launch_bounds__(32 * 9, 1) grow_kernel(const RunDev P) {
         __threadfence_block();
         atomicAdd(&head->done_warps, 1);
     }
+    }   // worker warps
+}
+
+template <int D, typename Key, int MODE>
+__global__ void __launch_bounds__(32 * 9, 1) grow_kernel(const __grid_constant__ RunDev P) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    grow_run<D, Key, MODE>(P, smem, nullptr, P.worker_warps * P.S);
+}
+
+// ---------------------------------------------------------------------------
+// Batch launch: R runs grown by one persistent grid.  Each CTA picks the open
+// run (tours left to start, walks left to grant) with the most tours left to
+// start per CTA already on it, weighted by n_max + 1, copies its descriptor to
+// shared memory, lays its shared memory out for that run and grows it until
+// the run is complete, or until its walks have no tickets left while another
+// run is open; then it picks again.  A run's tour-growing walks (at most one per
+// sequence, as in a single launch) are granted to the CTAs that join it.  With
+// no run open, a CTA joins an unfinished run (a stalled one first) as a helper
+// whose walks take waiting copies only.
+// ---------------------------------------------------------------------------
+// Returns the run to join (walks: how many of the CTA's walks grow tours), -1
+// when no run can take the CTA now, -2 when every run has finished or failed.
+__device__ int pick_run(const BatchDev &B, int &walks, bool &helper) {
+    int best = -1, stall = -1;
+    double best_s = -1.0, stall_s = -1.0;
+    bool best_open = false, unfinished = false;
+    for (int r = 0; r < B.R; ++r) {
+        const RunDev &Q = B.runs[r];
+        if (*(volatile int *)Q.status != 0) continue;
+        const long long lim = Q.tour_limit;
+        const long long f = (long long)*(volatile unsigned long long *)Q.finished;
+        if (f >= lim) continue;
+        unfinished = true;
+        const long long t = (long long)*(volatile unsigned long long *)Q.tickets;
+        const int a = *(volatile int *)(B.active + r);
+        const int g = *(volatile int *)(B.granted + r);
+        const double len = (double)(Q.n_max + 1);
+        // a run stalled on a large tour is the batch's critical path: among runs
+        // that take helpers it comes first, up to the CTAs its parts can use
+        const int fl = *(volatile int *)(B.closed + r);
+        if ((fl & kStalledBit) && Q.share && a * Q.worker_warps * Q.S < Q.share_boost) {
+            const double sc = (double)(lim - f) * len / (double)(a + 1);
+            if (sc > stall_s) { stall = r; stall_s = sc; }
+        }
+        if (t < lim) {
+            if (g < Q.n_seq) {
+                const double sc = (double)(lim - t) * len / (double)(a + 1);
+                if (!best_open || sc > best_s) { best = r; best_s = sc; best_open = true; }
+            }
+        } else if (!best_open && Q.share) {
+            const double sc = (double)(lim - f) * len / (double)(a + 1);
+            if (sc > best_s) { best = r; best_s = sc; }
+        }
+    }
+    walks = 0;
+    helper = false;
+    if (stall >= 0 && !best_open) best = stall;
+    if (best < 0) return unfinished ? -1 : -2;
+    const RunDev &Q = B.runs[best];
+    const int cap = Q.worker_warps * Q.S;
+    if (best_open) {
+        // grant up to a CTA's worth of walks, never more than one per sequence
+        for (int attempt = 0; attempt < 64; ++attempt) {
+            const int g = *(volatile int *)(B.granted + best);
+            const int k = Q.n_seq - g < cap ? Q.n_seq - g : cap;
+            if (k <= 0) break;
+            if (atomicCAS(B.granted + best, g, g + k) == g) {
+                walks = k;
+                if (g + k >= Q.n_seq && atomicOr(B.closed + best, 2) == 0) atomicSub(B.runs_open, 1);
+                break;
+            }
+        }
+        if (walks == 0) return -1;
+    } else {
+        walks = cap;                    // helper
+        helper = true;
+    }
+    atomicAdd(B.active + best, 1);
+    return best;
+}
+
+template <int MODE>
+__global__ void __launch_bounds__(32 * 9, 1) batch_kernel(const BatchDev B) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ RunDev Ps;
+    __shared__ int cur, walks, helping;
+    const long long t0 = global_ns();
+    for (;;) {
+        if (threadIdx.x == 0) {
+            int w = 0;
+            bool hp = false;
+            int r = pick_run(B, w, hp);
+            helping = hp ? 1 : 0;
+            if (r == -1 && global_ns() - t0 > B.max_ns) {
+                // the batch's time is up: every run not finished fails
+                for (int q = 0; q < B.R; ++q) {
+                    const RunDev &Q = B.runs[q];
+                    if ((long long)*(volatile unsigned long long *)Q.finished < Q.tour_limit)
+                        set_status(Q.status, PERM_ETIMEOUT);
+                }
+                r = -2;
+            }
+            cur = r;
+            walks = w;
+        }
+        __syncthreads();
+        const int r = cur;
+        if (r == -2) break;
+        if (r == -1) {
+            __nanosleep(8000);
+            __syncthreads();
+            continue;
+        }
+        const uint32_t *src = reinterpret_cast<const uint32_t *>(B.runs + r);
+        uint32_t *dst = reinterpret_cast<uint32_t *>(&Ps);
+        for (int i = threadIdx.x; i < (int)(sizeof(RunDev) / 4); i += blockDim.x) dst[i] = __ldcg(src + i);
+        __syncthreads();
+        const BatchLeave bl{B.runs_open, B.closed, B.active + r, helping != 0};
+        const int cw = walks;
+        if (Ps.d == 2) grow_run<2, uint32_t, MODE>(Ps, smem, &bl, cw);
+        else if (Ps.n_max > 512) grow_run<3, unsigned long long, MODE>(Ps, smem, &bl, cw);
+        else grow_run<3, uint32_t, MODE>(Ps, smem, &bl, cw);
+        __syncthreads();
+        if (threadIdx.x == 0) atomicSub(B.active + r, 1);
+        __syncthreads();
+    }
+}
+
+// Scheduling counters of a batch launch: nothing granted, no CTA on a run; a run
+// with no tours to grow counts as closed.
+__global__ void batch_init_kernel(const BatchDev B) {
+    __shared__ int open;
+    if (threadIdx.x == 0) open = 0;
+    __syncthreads();
+    for (int r = threadIdx.x; r < B.R; r += blockDim.x) {
+        const bool grows = B.runs[r].tour_limit > 0;
+        B.active[r] = 0;
+        B.granted[r] = 0;
+        B.closed[r] = grows ? 0 : 3;
+        if (grows) atomicAdd(&open, 1);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) *B.runs_open = open;
 }
 
 // ---------------------------------------------------------------------------
@@ -943,6 +1121,39 @@ cudaError_t launch_one(const RunDev &P, int ctas, cudaStream_t stream) {
     return cudaGetLastError();
 }
 }  // namespace
+
+cudaError_t batch_smem_budget(size_t *dynamic_max) {
+    int dev = 0, optin = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    cudaFuncAttributes fa;
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, batch_kernel<kSnapshot>);
+    if (e != cudaSuccess) return e;
+    const long long dyn = (long long)optin - (long long)fa.sharedSizeBytes;
+    if (dyn <= 0) return cudaErrorInvalidValue;
+    *dynamic_max = (size_t)dyn;
+    return cudaFuncSetAttribute(batch_kernel<kSnapshot>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
+}
+
+cudaError_t batch_grid(int threads, size_t smem, int *ctas) {
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_kernel<kSnapshot>, threads, smem);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) return cudaErrorInvalidConfiguration;
+    *ctas = sms * per_sm;
+    return cudaSuccess;
+}
+
+cudaError_t launch_batch(const BatchDev &B, int ctas, int threads, size_t smem, cudaStream_t stream) {
+    batch_init_kernel<<<1, 256, 0, stream>>>(B);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    batch_kernel<kSnapshot><<<ctas, threads, smem, stream>>>(B);
+    return cudaGetLastError();
+}
 
 cudaError_t set_smem_limits() {
     cudaError_t e = allow_smem<2, uint32_t, kSnapshot>();

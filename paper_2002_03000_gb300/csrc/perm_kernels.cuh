@@ -13,6 +13,7 @@ enum ThreshMode { kSnapshot = 0, kFresh = 1 };
 // Everything one persistent launch needs (passed by value).
 struct RunDev {
     int d, n_max, n_seq, alg;
+    int run_index;       // position in a batch launch's run table (0 otherwise)
     int log2h;           // per-walk hash size 2^log2h
     int S;               // lanes per warp that hold walks
     int stride;          // interleave stride of per-walk shared arrays (power of 2, >= S)
@@ -67,6 +68,35 @@ struct RunDev {
     int trace_cap;
     long long trace_every, trace_tour_every;
 };
+
+// One launch growing several runs (snapshot form of Alg. 2): the runs' descriptors
+// in device memory and the scheduling counters.
+struct BatchDev {
+    const RunDev *runs;   // R descriptors; run r's run_index is r
+    int R;
+    int *active;          // per run: CTAs on it now
+    int *granted;         // per run: tour-growing walks handed to CTAs
+    int *runs_open;       // runs with tours to start and walks to grant
+    int *closed;          // per run: bit 0 tickets exhausted, bit 1 walks all granted
+    long long max_ns;     // wall-clock bound of the launch
+};
+
+// Largest dynamic shared memory a batch CTA can have (and allow it).
+cudaError_t batch_smem_budget(size_t *dynamic_max);
+// CTAs of a batch launch: every SM, as many CTAs each as fit.
+cudaError_t batch_grid(int threads, size_t smem, int *ctas);
+// Counters reset, then the persistent batch kernel.
+cudaError_t launch_batch(const BatchDev &B, int ctas, int threads, size_t smem, cudaStream_t stream);
+
+// Host side of batch members (runs whose descriptors sit in a batch's table):
+// a run laid out for `ctas` CTAs of at most 4 x 8 walks within smem_budget bytes
+// of shared memory, and its descriptor for tours_per_seq tours per sequence from
+// empty tables.
+int member_create(perm_handle *out, const perm_config *cfg, int ctas, size_t smem_budget);
+int member_params(perm_handle h, int64_t tours_per_seq, int run_index, RunDev *P, size_t *smem,
+                  int *worker_warps);
+// Empty tables and tour sums (every row, also after a failed run), on the run's stream.
+int member_reset(perm_handle h);
 
 // Shared-memory bytes of one CTA.
 size_t cta_smem_bytes(int d, bool key64, int n_max, int log2h, int stack_cache, int worker_warps,
