@@ -170,12 +170,14 @@ def cpu_baseline(seconds=15.0):
 
 
 def batched_vs_plain(tours):
-    """The batched form against the plain per-run form, on the same runs and tours
-    (hence the same expected error): 96 independent runs with d uniform in {2, 3},
-    n_max log-uniform in [64, 2048] and sequences log-uniform in [256, 8192]
-    (PCG64 seed 1).  Batched: every run's reset and growth captured in one CUDA
-    graph, the runs' kernels concurrent on 64 streams.  Plain: each run alone on
-    the whole GPU, one after another.  Wall time with the device synchronised."""
+    """The batched forms against the plain per-run form, on the same runs and tours
+    (the same estimator; its error is reported beside the time): 96 independent runs
+    with d uniform in {2, 3}, n_max log-uniform in [64, 2048] and sequences
+    log-uniform in [256, 8192] (PCG64 seed 1).  Batched, streams: every run's reset
+    and growth kernel captured in one CUDA graph, the runs' kernels concurrent on 64
+    streams.  Batched, persistent: one persistent kernel on every SM grows all runs
+    (captured in a CUDA graph with the resets).  Plain: each run alone on the whole
+    GPU, one after another.  Wall time with the device synchronised."""
     import numpy as np
     import torch
     import paper_2002_03000_gb300 as pg
@@ -185,20 +187,23 @@ def batched_vs_plain(tours):
     out = {"workload": "96 independent runs: d uniform in {2,3}, n_max log-uniform in [64,2048], "
                        "sequences log-uniform in [256,8192] (PCG64 seed 1), %d tours per sequence" % tours,
            "tours_per_seq": tours}
-    b = pb.Batch(cfgs, [tours] * len(runs))
-    try:
-        b.run()                                   # warm-up (and first replay)
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        b.run()
-        tb = time.perf_counter() - t0
-        steps_b = sum(b.stats(r)["steps"] for r in range(len(runs)))
-        rel_b = [math.sqrt(b.estimates(r)[2][runs[r][1]]) for r in range(len(runs))]
-    except Exception as e:                        # report, do not hide
-        b.close()
-        out["error"] = str(e)
-        return out
-    b.close()
+    forms = {}
+    for form in ("streams", "persistent"):
+        b = pb.Batch(cfgs, [tours] * len(runs), persistent=(form == "persistent"))
+        try:
+            b.run()                                   # warm-up (and first replay)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            b.run()
+            tb = time.perf_counter() - t0
+            steps_b = sum(b.stats(r)["steps"] for r in range(len(runs)))
+            rel_b = [math.sqrt(b.estimates(r)[2][runs[r][1]]) for r in range(len(runs))]
+            forms[form] = {"seconds": tb, "steps_per_s": steps_b / tb, "steps": steps_b,
+                           "median_rel_se_c_nmax": float(np.median(rel_b))}
+        except Exception as e:                    # report, do not hide
+            forms[form] = {"error": str(e)}
+        finally:
+            b.close()
     hs = [pg.Run(d, n, N, 1, run_id=i, max_seconds=120.0) for i, (d, n, N) in enumerate(runs)]
     torch.cuda.synchronize()
     t0 = time.perf_counter()
@@ -213,11 +218,18 @@ def batched_vs_plain(tours):
     tp = time.perf_counter() - t0
     for h in hs:
         h.close()
-    out.update({"batched_s": tb, "plain_s": tp, "speedup": tp / tb,
-                "batched_steps_per_s": steps_b / tb, "plain_steps_per_s": steps_p / tp,
-                "median_rel_se_c_nmax": {"batched": float(np.median(rel_b)), "plain": float(np.median(rel_p))},
-                "plain_failed": failed,
+    plain = {"seconds": tp, "steps_per_s": steps_p / tp, "steps": steps_p,
+             "median_rel_se_c_nmax": float(np.median(rel_p)) if rel_p else None, "failed": failed}
+    out.update({"streams": forms["streams"], "persistent": forms["persistent"], "plain": plain,
                 "timing": "wall clock around one graph replay / the 96 plain runs, device synchronised"})
+    for form in ("streams", "persistent"):
+        f = forms[form]
+        if "seconds" in f:
+            f["speedup_vs_plain"] = tp / f["seconds"]
+            if plain["median_rel_se_c_nmax"]:
+                # time to the plain form's error, the variance falling as 1/tours
+                f["speedup_vs_plain_at_equal_error"] = tp / (f["seconds"] * (f["median_rel_se_c_nmax"] /
+                                                                            plain["median_rel_se_c_nmax"]) ** 2)
     return out
 
 
