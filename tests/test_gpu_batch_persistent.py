@@ -13,7 +13,7 @@ import pytest
 import paper_2002_03000_gb300 as pg
 from paper_2002_03000_gb300 import batch as pb
 from paper_2002_03000_gb300 import _native as nat
-from tests.gpu_util import torch_cuda
+from tests.gpu_util import SIGMA_FLOOR, torch_cuda
 
 pytestmark = pytest.mark.gpu
 
@@ -46,8 +46,11 @@ def test_persistent_batch_counting_theorem_and_replay(exact_counts):
 
 
 def test_persistent_batch_agrees_with_alone():
-    """The same run in a persistent batch and alone: log c_n agree within the
-    combined standard errors at every length (z-scores over all lengths)."""
+    """The same run in a persistent batch and alone (other seeds): log c_n agree
+    within the combined standard errors.  The z-scores of neighbouring lengths are
+    strongly correlated (one tour's fluctuation moves all of them), so their mean
+    over lengths is about one standard normal draw: both it and the largest |z|
+    get bounds that a real bias of a few standard errors breaks."""
     torch_cuda()
     spec = [(2, 200, 2000, 8), (3, 150, 1500, 8), (2, 64, 500, 30)]
     cfgs = [pb.make_config(d, n, N, 31 + i, max_seconds=120.0) for i, (d, n, N, _) in enumerate(spec)]
@@ -59,9 +62,9 @@ def test_persistent_batch_agrees_with_alone():
                 run.run(t)
                 lca, Sa, rva = run.estimates()
             ok = np.isfinite(lca) & np.isfinite(lcb) & (rva > 0) & (rvb > 0)
-            z = (lcb[ok] - lca[ok]) / np.sqrt(rva[ok] + rvb[ok])
-            assert np.mean(np.abs(z) > 3.5) < 0.02, (r, np.max(np.abs(z)))
-            assert abs(np.mean(z)) < 1.0, (r, np.mean(z))
+            z = (lcb[ok] - lca[ok]) / np.sqrt(rva[ok] + rvb[ok] + 2 * SIGMA_FLOOR ** 2)
+            assert np.max(np.abs(z)) < 5.0, (r, np.max(np.abs(z)))
+            assert abs(np.mean(z)) < 3.5, (r, np.mean(z))
 
 
 def test_persistent_batch_mixed_workload_completes():
