@@ -36,6 +36,8 @@ def configure(L):
     L.orc_create.argtypes = [C.POINTER(C.c_void_p), C.c_int, C.c_int, C.c_int,
                              C.c_uint64, C.c_uint32, C.c_int]
     L.orc_run.argtypes = [C.c_void_p, C.c_int64]
+    L.orc_set_cutoffs.argtypes = [C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_double),
+                                  C.c_int, C.c_double]
     dp = C.POINTER(C.c_double)
     i64p = C.POINTER(C.c_int64)
     L.orc_tables.argtypes = [C.c_void_p, dp, dp, dp, i64p, i64p, i64p]
@@ -118,6 +120,19 @@ class Oracle:
         if rc != 0:
             raise ValueError("orc_create failed: %d" % rc)
         self._h = h
+
+    def set_cutoffs(self, T_hi, t_lo, copies=2, q=2.0):
+        """Original PERM (Sec. 2): cut-offs per length at the stored scale (None,
+        None: back to flatPERM)."""
+        if T_hi is None and t_lo is None:
+            rc = lib().orc_set_cutoffs(self._h, None, None, 0, 0.0)
+        else:
+            hi = np.ascontiguousarray(T_hi, dtype=np.float64)
+            lo = np.ascontiguousarray(t_lo, dtype=np.float64)
+            assert hi.shape == lo.shape == (self.n_max + 1,)
+            rc = lib().orc_set_cutoffs(self._h, _p(hi, C.c_double), _p(lo, C.c_double), int(copies), float(q))
+        if rc != 0:
+            raise RuntimeError("orc_set_cutoffs failed: %d" % rc)
 
     def run(self, tours_per_seq):
         rc = lib().orc_run(self._h, tours_per_seq)

@@ -24,6 +24,13 @@
  *    c_n from orc_enumerate), by weight conservation under enrichment, by the
  *    survival probability of pruning, and by the uniformity of the chosen
  *    directions.
+ *  - original PERM with cut-offs (orc_set_cutoffs; Sec. 2, the paragraphs on
+ *    T_k, t_k and q): pinned by its special cases -- no cut-off active is the
+ *    Rosenbluth method (one sample per length per tour, exact c_2 and c_3 per
+ *    tour); always enrich gives the deterministic tree of 2^(n-1) samples with
+ *    exact c_2, c_3; always prune makes the survivors at n = 2 binomial with
+ *    probability 1/q and each carry exactly q 12 -- and by the counting
+ *    theorem with cut-offs active on both sides.
  *  - variance estimate: per-tour sums (the paper gives no error bars); pinned
  *    by the z-score calibration of the estimates against exact c_n over many
  *    seeds.
@@ -254,9 +261,23 @@ typedef struct {
     uint64_t survive_K;
 } node_out;
 
+/* Original PERM (Sec. 2, the cut-offs T_k and t_k): a node of weight W above
+ * T_n is enriched into `copies` copies of weight W/copies, one below t_n is
+ * pruned with probability 1 - 1/q and otherwise carries q W.  Cut-offs are at
+ * the stored weight scale.  Readings: the copies take distinct steps, at most
+ * a_+ of them, each carrying W/c for the c made (as flatPERM's copies); the
+ * survival probability is 1/q rounded to single precision, taken as the
+ * integer threshold K = ceil((1/q) 2^32), and the survivor carries W 2^32/K;
+ * the empty walk is neither enriched nor pruned. */
+typedef struct {
+    const double *hi, *lo;   /* T_n and t_n, n = 0..n_max */
+    float r_hi, r_lo;        /* copies, and 1/q in single precision */
+} perm_cuts;
+
 static int grow_node(int d, int n_max, int n, const int32_t *end, const occset *occ,
                      double W, double T, int64_t M, uint64_t ordinal, uint32_t seq,
-                     uint32_t tour, uint64_t seed, uint32_t run, node_out *o) {
+                     uint32_t tour, uint64_t seed, uint32_t run, const perm_cuts *cuts,
+                     node_out *o) {
     o->a_plus = 0; o->free_mask = 0; o->c = 0; o->r = 0.0f; o->child_w = 0.0;
     o->survive_K = 0;
     if (n == n_max) return ORC_LEAF_NMAX;                     /* walk complete */
@@ -276,6 +297,13 @@ static int grow_node(int d, int n_max, int n, const int32_t *end, const occset *
 
     /* r (Sec. 2, eq. 6) and the node's random block */
     float r = orc_ratio(n, W, T, M);
+    if (cuts && n > 0) {
+        /* original PERM: the same decision rules with r = copies (enrich: c copies
+         * of W/c), r = 1/q (prune: survive with probability 1/q, weight q W) or 1 */
+        if (W > cuts->hi[n]) r = cuts->r_hi;
+        else if (W < cuts->lo[n]) r = cuts->r_lo;
+        else r = 1.0f;
+    }
     o->r = r;
     uint32_t ctr[4] = {(uint32_t)ordinal, (uint32_t)(ordinal >> 32), tour, seq};
     uint32_t key[2] = {(uint32_t)seed ^ run, (uint32_t)(seed >> 32)};
@@ -341,7 +369,7 @@ int orc_step(int d, int n_max, int n, const int32_t *coords, double W, double T,
     occ.d = d; occ.n_max = n_max; occ.box = NULL; occ.coords = coords; occ.n = n;
     node_out o;
     int rc = grow_node(d, n_max, n, coords + (long)n * d, &occ, W, T, M, ordinal, seq,
-                       tour, seed, run, &o);
+                       tour, seed, run, NULL, &o);
     if (a_plus) *a_plus = o.a_plus;
     if (free_mask) *free_mask = o.free_mask;
     if (r) *r = o.r;
@@ -374,12 +402,15 @@ struct orc_state {
     long stack_cap;
     occset occ;
     int64_t steps, max_stack;
+    double *cut_hi, *cut_lo;   /* original PERM's cut-offs (NULL: flatPERM) */
+    perm_cuts cuts;
 };
 
 void orc_destroy(orc_state *h) {
     if (!h) return;
     free(h->Wn); free(h->Qn); free(h->Rn); free(h->Sn); free(h->M); free(h->tours_done);
     free(h->X); free(h->coords); free(h->stack); free(h->occ.box);
+    free(h->cut_hi); free(h->cut_lo);
     free(h);
 }
 
@@ -449,7 +480,7 @@ static int run_tour(orc_state *h, int tab, uint32_t seq, uint32_t tour, int64_t 
         h->steps += 1;
         node_out o;
         int rc = grow_node(d, n_max, n, co + (long)n * d, &h->occ, W, T, M, ordinal,
-                           seq, tour, h->seed, h->run, &o);
+                           seq, tour, h->seed, h->run, h->cut_hi ? &h->cuts : NULL, &o);
         ordinal += 1;
         if (rc == ORC_CHILDREN) {
             /* copies 1..c-1 wait on the stack (copy 1 on top); copy 0 grows now */
@@ -486,6 +517,30 @@ static int run_tour(orc_state *h, int tab, uint32_t seq, uint32_t tour, int64_t 
         Qn[k] += h->X[k] * h->X[k];
         h->X[k] = 0.0;
     }
+    return ORC_OK;
+}
+
+int orc_set_cutoffs(orc_state *h, const double *T_hi, const double *t_lo, int copies, double q) {
+    if (!h) return ORC_EINVAL;
+    free(h->cut_hi); free(h->cut_lo);
+    h->cut_hi = h->cut_lo = NULL;
+    if (!T_hi && !t_lo) return ORC_OK;                         /* back to flatPERM */
+    if (!T_hi || !t_lo || copies < 1 || copies > 2 * h->d || !(q >= 1.0) || q > 4294967296.0)
+        return ORC_EINVAL;
+    size_t L = (size_t)h->n_max + 1;
+    h->cut_hi = (double *)malloc(L * sizeof(double));
+    h->cut_lo = (double *)malloc(L * sizeof(double));
+    if (!h->cut_hi || !h->cut_lo) {
+        free(h->cut_hi); free(h->cut_lo);
+        h->cut_hi = h->cut_lo = NULL;
+        return ORC_ENOMEM;
+    }
+    memcpy(h->cut_hi, T_hi, L * sizeof(double));
+    memcpy(h->cut_lo, t_lo, L * sizeof(double));
+    h->cuts.hi = h->cut_hi;
+    h->cuts.lo = h->cut_lo;
+    h->cuts.r_hi = (float)copies;
+    h->cuts.r_lo = (float)(1.0 / q);
     return ORC_OK;
 }
 

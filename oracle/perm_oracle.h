@@ -65,6 +65,13 @@ typedef struct orc_state orc_state;
 /* A flatPERM simulation: d, n_max, N sequences, seed, run id, algorithm. */
 int orc_create(orc_state **out, int d, int n_max, int n_seq, uint64_t seed,
                uint32_t run, int alg);
+/* Original PERM with cut-offs (Sec. 2): from now on a node of length n >= 1 and
+ * weight W > T_hi[n] is enriched into `copies` copies (distinct steps, at most
+ * a_+, each W/c), one with W < t_lo[n] survives with probability 1/q (in
+ * single precision) and then carries q W; the shared table no longer decides.
+ * T_hi, t_lo: n_max+1 doubles at the stored scale, copied.  copies in
+ * 1..2d, q >= 1.  Both NULL: back to flatPERM. */
+int orc_set_cutoffs(orc_state *h, const double *T_hi, const double *t_lo, int copies, double q);
 /* Continue the simulation by tours_per_seq tours of every sequence. */
 int orc_run(orc_state *h, int64_t tours_per_seq);
 /* Raw tables (stored scale): W_n, S_n, Q_n over n = 0..n_max (Alg. 2), or the

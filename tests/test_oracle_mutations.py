@@ -40,6 +40,9 @@ MUTATIONS = {
                                         "const int64_t x = co[(long)(n > 0 ? n - 1 : 0) * d + i];"),
     "observable not squared": ("r2 += x * x;", "r2 += x < 0 ? -x : x;"),
     "observable unweighted": ("Rn[n] += W * (double)r2;", "Rn[n] += (double)r2;"),
+    "cut-off comparison inverted": ("if (W > cuts->hi[n]) r = cuts->r_hi;", "if (W < cuts->hi[n]) r = cuts->r_hi;"),
+    "cut-off survival probability q, not 1/q": ("h->cuts.r_lo = (float)(1.0 / q);", "h->cuts.r_lo = (float)q;"),
+    "cut-offs applied at the empty walk": ("if (cuts && n > 0) {", "if (cuts) {"),
 }
 
 
@@ -123,6 +126,32 @@ def _pins_hold(exact2):
             zs.append((math.exp(lc[10] - math.log(exact2[10])) - 1.0) / math.sqrt(rv[10]))
     sd = float(np.std(zs))
     if not (0.4 < sd < 2.5):
+        return False
+    # original PERM with cut-offs (Sec. 2): no cut-off active is Rosenbluth, always
+    # enriching grows a fixed tree, always pruning is binomial with exact reweighting
+    h = orc.Oracle(2, 8, 2, seed=21)
+    h.set_cutoffs(np.full(9, np.inf), np.zeros(9), 2, 2.0)
+    h.run(300)
+    t = h.tables()
+    if t["max_stack"] != 0 or not np.all(t["S"][:7] == 600):
+        return False
+    h = orc.Oracle(2, 3, 1, seed=5)
+    h.set_cutoffs(np.zeros(4), np.zeros(4), 3, 2.0)
+    h.run(20)
+    if list(h.tables()["S"]) != [20, 20, 60, 180]:
+        return False
+    lc, S, rv = h.estimates()
+    if not (math.isclose(math.exp(lc[2]), 12.0, rel_tol=1e-12) and math.isclose(math.exp(lc[3]), 36.0, rel_tol=1e-12)):
+        return False
+    h = orc.Oracle(2, 3, 4, seed=77)
+    h.set_cutoffs(np.full(4, np.inf), np.full(4, np.inf), 2, 3.0)
+    h.run(2500)
+    t = h.tables()
+    K = math.ceil(float(np.float32(1.0 / 3.0)) * 2.0 ** 32)
+    p, M, S2 = K / 2.0 ** 32, 10000, t["S"][2]
+    if abs(S2 - M * p) > 5.0 * math.sqrt(M * p * (1 - p)):
+        return False
+    if not math.isclose(t["W"][2], S2 * 12.0 * (2.0 ** 32 / K) * 2.0 ** -orc.scale_exp(2, 2), rel_tol=1e-12):
         return False
     # the observable estimator (Sec. 1, eq. 5) against the exact mean |omega_n|^2
     c, r2 = orc.enumerate_r2(2, 10)
