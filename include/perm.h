@@ -106,6 +106,25 @@ int perm_create_ex(perm_handle *out, const perm_config *cfg);
 /* Queue all later work of h on `stream` (a cudaStream_t; NULL = legacy default). */
 int perm_set_stream(perm_handle h, void *stream);
 
+/* Original PERM with cut-offs (Sec. 2, the paragraphs on T_k, t_k and q)
+ * instead of flatPERM's ratio, for the runs that follow:
+ *   - a node of length n >= 1 whose weight W exceeds T_hi[n] is enriched into
+ *     `copies` copies, with distinct steps, at most a_+ of them, each carrying
+ *     W/c for the c made;
+ *   - one with W < t_lo[n] survives with probability 1/q (1/q rounded to single
+ *     precision and taken as the integer threshold K = ceil((1/q) 2^32) on the
+ *     node's first random word) and then carries W 2^32/K (= q W when 1/q is
+ *     exact in single precision);
+ *   - otherwise it grows one copy, as in flatPERM with r = 1.
+ * The empty walk is neither enriched nor pruned.  The shared table no longer
+ * decides anything, so a run with sharing off (fresh thresholds, or
+ * share_copies = -1) is deterministic for any number of sequences.
+ * T_hi, t_lo: host arrays of n_max+1 doubles at the stored weight scale (the
+ * scale of perm_tables' W_n; e.g. a multiple of W_n/M from an earlier run),
+ * copied before return.  copies in 1..2d; 1 <= q <= 2^32.  Both arrays NULL:
+ * back to flatPERM.  PERM_EINVAL on a bad argument. */
+int perm_set_cutoffs(perm_handle h, const double *T_hi, const double *t_lo, int copies, double q);
+
 /* Grow tours_per_seq more tours of every sequence (cumulative: repeated calls
  * continue the same tables, tour counters and random streams).  Queues one
  * persistent kernel launch and returns without waiting unless `sync` is set

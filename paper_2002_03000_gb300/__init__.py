@@ -34,6 +34,15 @@ class Run:
         self.d, self.n_max, self.n_seq, self.alg = d, n_max, n_seq, alg
         self.h = _native.perm_create_ex(cfg)
 
+    def set_cutoffs(self, T_hi, t_lo, copies=2, q=2.0):
+        """Original PERM (Sec. 2) from now on: enrich into `copies` copies above
+        T_hi[n], prune with probability 1 - 1/q below t_lo[n] (both n_max+1
+        values at the stored weight scale); None, None: back to flatPERM."""
+        if T_hi is not None or t_lo is not None:
+            if len(T_hi) != self.n_max + 1 or len(t_lo) != self.n_max + 1:
+                raise ValueError("cut-offs need n_max + 1 values each")
+        _native.perm_set_cutoffs(self.h, T_hi, t_lo, copies, q)
+
     def run(self, tours_per_seq, sync=True):
         if sync:
             _native.perm_run_sync(self.h, tours_per_seq)

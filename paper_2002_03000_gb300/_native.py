@@ -33,7 +33,7 @@ EXPORTS = (
     "perm_config_init", "perm_create", "perm_create_ex", "perm_set_stream", "perm_run", "perm_reset",
     "perm_run_sync", "perm_estimates", "perm_tables", "perm_stats", "perm_trace_enable",
     "perm_trace_read", "perm_destroy", "perm_strerror", "perm_debug_step", "perm_debug_philox",
-    "perm_run_static", "perm_batch_create", "perm_batch_create_persistent", "perm_batch_run", "perm_batch_size",
+    "perm_run_static", "perm_set_cutoffs", "perm_batch_create", "perm_batch_create_persistent", "perm_batch_run", "perm_batch_size",
     "perm_batch_estimates", "perm_batch_stats", "perm_batch_destroy", "perm_autotune",
     "perm_observable_r2",
 )
@@ -110,6 +110,7 @@ def load(path: str = LIB_PATH):
     L.perm_debug_philox.argtypes = [C.c_int, vp, C.POINTER(u32), vp]
     L.perm_run_static.argtypes = [C.POINTER(perm_config), i64, vp, vp, vp, C.POINTER(i64), vp]
     L.perm_batch_create.argtypes = [hp, C.POINTER(perm_config), C.POINTER(i64), C.c_int, C.c_int]
+    L.perm_set_cutoffs.argtypes = [vp, dp, dp, C.c_int, C.c_double]
     L.perm_batch_create_persistent.argtypes = [hp, C.POINTER(perm_config), C.POINTER(i64), C.c_int]
     L.perm_batch_run.argtypes = [vp]
     L.perm_batch_size.argtypes = [vp]
@@ -251,6 +252,18 @@ def perm_batch_create(cfgs, tours, n_streams=0):
     b = C.c_void_p()
     _check(load().perm_batch_create(C.byref(b), arr, t, R, n_streams), "perm_batch_create")
     return b
+
+
+def perm_set_cutoffs(h, T_hi, t_lo, copies=2, q=2.0):
+    """Original PERM cut-offs (stored scale, n_max+1 each); None, None: flatPERM."""
+    if T_hi is None and t_lo is None:
+        _check(load().perm_set_cutoffs(h, None, None, 0, 0.0), "perm_set_cutoffs")
+        return
+    hi = np.ascontiguousarray(T_hi, dtype=np.float64)
+    lo = np.ascontiguousarray(t_lo, dtype=np.float64)
+    if hi.shape != lo.shape:
+        raise ValueError("cut-off arrays differ in length")
+    _check(load().perm_set_cutoffs(h, _dp(hi), _dp(lo), int(copies), float(q)), "perm_set_cutoffs")
 
 
 def perm_batch_create_persistent(cfgs, tours):

@@ -43,6 +43,8 @@ struct perm_run_s {
     unsigned long long *dq_head = nullptr, *dq_tail = nullptr;
     unsigned int *dq_ready = nullptr, *dq_free = nullptr, *outst = nullptr, *tmaxn = nullptr;
     int *hungry = nullptr;
+    double2 *cut = nullptr;        // original PERM's cut-offs (nullptr: flatPERM)
+    float r_hi = 1.0f, r_lo = 1.0f;
     perm_trace_record *trace = nullptr;
     int32_t *trace_coords = nullptr;
     int trace_cap = 0;
@@ -77,7 +79,7 @@ void free_all(perm_handle h) {
     void *ptrs[] = {h->Wn, h->Qn, h->Rn, h->X, h->gstk_w, h->Sn, h->tickets, h->seq_M, h->steps,
                     h->max_stack, h->copies, h->refreshes, h->iterations, h->finished, h->trace_count, h->gstk_meta, h->status, h->trace,
                     h->trace_coords, h->dq_cells, h->dq_head, h->dq_tail, h->dq_ready, h->dq_free, h->outst,
-                    h->tmaxn, h->hungry};
+                    h->tmaxn, h->hungry, h->cut};
     for (void *p : ptrs) if (p) cudaFree(p);
 }
 
@@ -372,11 +374,41 @@ static RunDev make_params(perm_handle h) {
     P.dq_head = h->dq_head; P.dq_tail = h->dq_tail; P.dq_ready = h->dq_ready; P.dq_free = h->dq_free;
     P.outst = h->outst; P.tmaxn = h->tmaxn; P.hungry = h->hungry;
     P.status = h->status;
+    P.cut = h->cut; P.r_hi = h->r_hi; P.r_lo = h->r_lo;
     P.trace = (h->trace_every > 0) ? h->trace : nullptr;
     P.trace_coords = h->trace_coords; P.trace_count = h->trace_count; P.trace_cap = h->trace_cap;
     P.trace_every = h->trace_every > 0 ? h->trace_every : 1;
     P.trace_tour_every = h->trace_tour_every > 0 ? h->trace_tour_every : 1;
     return P;
+}
+
+int perm_set_cutoffs(perm_handle h, const double *T_hi, const double *t_lo, int copies, double q) {
+    if (!h) return PERM_EINVAL;
+    if (!T_hi && !t_lo) {                                   // back to flatPERM
+        if (h->cut) {
+            if (cudaStreamSynchronize(h->stream) != cudaSuccess) return PERM_EDEVICE;
+            cudaFree(h->cut);
+            h->device_bytes -= (long long)(sizeof(double2) * ((size_t)h->cfg.n_max + 1));
+        }
+        h->cut = nullptr;
+        return PERM_OK;
+    }
+    if (!T_hi || !t_lo || copies < 1 || copies > 2 * h->cfg.d || !(q >= 1.0) || q > 4294967296.0)
+        return PERM_EINVAL;
+    const size_t L = (size_t)h->cfg.n_max + 1;
+    std::vector<double2> host(L);
+    for (size_t k = 0; k < L; ++k) host[k] = make_double2(T_hi[k], t_lo[k]);
+    if (!h->cut) {
+        const int rc = dalloc(h, &h->cut, L);
+        if (rc != PERM_OK) return rc;
+    }
+    // the copy is ordered on the handle's stream, after any launch already queued
+    cudaError_t e = cudaMemcpyAsync(h->cut, host.data(), sizeof(double2) * L, cudaMemcpyHostToDevice, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return to_code(e);
+    h->r_hi = (float)copies;
+    h->r_lo = (float)(1.0 / q);
+    return PERM_OK;
 }
 
 int perm_run(perm_handle h, int64_t tours_per_seq) {

@@ -123,13 +123,22 @@ __device__ __forceinline__ NodeOut grow_node(const Key *hash, int stride, int la
                                              unsigned long long Tp, unsigned long long M,
                                              unsigned long long ordinal, uint32_t seq,
                                              uint32_t tour, uint32_t k0, uint32_t k1,
-                                             const double *aoc, int (&eslot)[2 * D]) {
+                                             const double *aoc, int (&eslot)[2 * D],
+                                             const double2 *cut = nullptr, float r_hi = 1.0f,
+                                             float r_lo = 1.0f) {
     NodeOut o;
     o.a = 0; o.mask = 0; o.child_w = 0.0; o.overflow = false;
     o.dec.c = 0; o.dec.dirs = 0u; o.dec.F = 0.0;
     // three independent chains: the node's random block, r, and the probes
     const Philox4 w = philox4x32_10((uint32_t)ordinal, (uint32_t)(ordinal >> 32), tour, seq, k0, k1);
-    const float r = ratio_r(n, W, Tp, M);
+    float r = ratio_r(n, W, Tp, M);
+    if (cut != nullptr && n > 0) {
+        // original PERM (Sec. 2, cut-offs T_n, t_n): the same decision rules with
+        // r = copies above T_n (c copies of W/c), r = 1/q below t_n (survive with
+        // probability 1/q, weight q W), r = 1 between them
+        const double2 tc = __ldg(cut + n);
+        r = W > tc.x ? r_hi : (W < tc.y ? r_lo : 1.0f);
+    }
     o.r = r;
     if (n == n_max) { o.outcome = kLeafNmax; return o; }
     bool ovf = false;
@@ -612,7 +621,8 @@ __device__ __forceinline__ void grow_run(const RunDev &P, unsigned char *smem, c
 #pragma unroll
             for (int j = 0; j < 2 * D; ++j) eslot[j] = 0;
             const NodeOut o = grow_node<D, Key>(hash, ST, lane, P.log2h, n, P.n_max, cx, cy, cz, W, Tp,
-                                                Mb, ordinal, seq, tour, P.key0, P.key1, aoc, eslot);
+                                                Mb, ordinal, seq, tour, P.key0, P.key1, aoc, eslot,
+                                                P.cut, P.r_hi, P.r_lo);
             if (o.overflow) set_status(P.status, PERM_EOVERFLOW);
 
             if (P.trace != nullptr && (ordinal % (unsigned long long)P.trace_every) == 0ull &&

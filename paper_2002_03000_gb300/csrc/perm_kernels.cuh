@@ -30,6 +30,10 @@ struct RunDev {
     unsigned long long *Sn;
     double *Qn;
     double *Rn;                    // optional (nullptr: off): sum of W |omega_n|^2 per length
+    // original PERM (nullptr: flatPERM): per length (T_n, t_n) at the stored scale; a node
+    // above T_n decides with r = r_hi (copies), one below t_n with r = r_lo (1/q)
+    const double2 *cut;
+    float r_hi, r_lo;
     unsigned long long *tickets;   // Alg. 2: tours started (M); Alg. 1: next sequence
     unsigned long long *seq_M;     // Alg. 1: tours done per sequence
     // per-walk scratch

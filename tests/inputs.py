@@ -99,3 +99,25 @@ def shortest_trapped_walk_2d(max_len=8):
         if res:
             return np.array(res, dtype=np.int32)
     return None
+
+
+# growth constants and amplitude exponents of c_n ~ A mu^n n^(gamma - 1) from the
+# literature (square: mu = 2.63815853, gamma = 43/32; cubic: mu = 4.6840386,
+# gamma = 1.1570), used only to place cut-offs of the original PERM near c_n
+_ASYMPTOTICS = {2: (2.63815853, 43.0 / 32.0, 1.18), 3: (4.6840386, 1.1570, 1.21)}
+
+
+def perm_cutoffs(d, n_max, f, scale_exp):
+    """Cut-offs T_n = f a_n and t_n = a_n / f around the asymptotic form a_n of
+    c_n, at the stored weight scale 2^-scale_exp(n) (the scale function is passed
+    in, so that this module holds none of the method's arithmetic)."""
+    import math
+    mu, gamma, amp = _ASYMPTOTICS[d]
+    hi = np.empty(n_max + 1)
+    lo = np.empty(n_max + 1)
+    for n in range(n_max + 1):
+        # in logs: mu^n alone leaves the double range at long lengths
+        la = math.log(amp) + n * math.log(mu) + (gamma - 1.0) * math.log(max(n, 1)) - scale_exp(n) * math.log(2.0)
+        hi[n] = f * math.exp(la)
+        lo[n] = math.exp(la) / f
+    return hi, lo
