@@ -289,6 +289,43 @@ def growth_constants(sq_estimates):
     return out
 
 
+def perm_cutoffs_vs_flatperm(tours=32):
+    """Original PERM (Sec. 2, fixed cut-offs) against flatPERM on the bench lattice
+    (square, n_max 512, 4096 sequences).  Cut-offs from a pilot flatPERM run of 8
+    tours per sequence: T_n = 3 W^_n and t_n = W^_n / 3 with W^_n = W_n / M at the
+    stored scale; 2 copies, q = 2.  Then `tours` tours per sequence of each from
+    empty tables.  Wall time with the device synchronised; relative standard error
+    of c_512 from the per-tour variance."""
+    import numpy as np
+    import torch
+    import paper_2002_03000_gb300 as pg
+    d, n_max, N = 2, 512, 4096
+    out = {"workload": "square lattice, n_max 512, 4096 sequences x %d tours; PERM cut-offs 3x and 1/3x "
+                       "W_n/M of a pilot flatPERM run (8 tours/sequence), 2 copies, q = 2" % tours}
+    with pg.Run(d, n_max, N, 3, max_seconds=120.0) as pilot:
+        pilot.run(8)
+        t = pilot.tables()
+    w_hat = t["W"] / float(t["M"][0])
+    if not np.all(w_hat > 0):
+        out["error"] = "pilot run left lengths unsampled"
+        return out
+    for form in ("flatperm", "perm_cutoffs"):
+        with pg.Run(d, n_max, N, 1, max_seconds=120.0) as run:
+            if form == "perm_cutoffs":
+                run.set_cutoffs(3.0 * w_hat, w_hat / 3.0, 2, 2.0)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            run.run(tours)
+            sec = time.perf_counter() - t0
+            lc, S, rv = run.estimates()
+            st = run.stats()
+        out[form] = {"seconds": sec, "steps": st["steps"], "steps_per_s": st["steps"] / sec,
+                     "log_c_nmax": float(lc[n_max]),
+                     "rel_se_c_nmax": float(math.sqrt(rv[n_max])) if rv[n_max] > 0 else None,
+                     "samples_at_nmax": float(S[n_max])}
+    return out
+
+
 def alg1_vs_alg2():
     """Sec. 4's comparison on the exact-count lattice (square, n_max 16, 12
     sequences): T_16, the mean |log c_n(exact) - log c_n(estimate)| over n = 1..16,
@@ -536,6 +573,7 @@ def run_ours(args):
     if world == 1 and not args.skip_systems:
         line["growth_constant"] = growth_constants((lc, rv))
         line["alg1_vs_alg2"] = alg1_vs_alg2()
+        line["perm_cutoffs"] = perm_cutoffs_vs_flatperm()
         line["autotune"] = autotuned_run(w["tours"])
         line["batched"] = batched_vs_plain(args.batch_tours)
         line["served"] = served_vs_one_at_a_time()
