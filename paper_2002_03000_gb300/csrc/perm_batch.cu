@@ -175,8 +175,11 @@ int perm_batch_create_persistent(perm_batch_handle *out, const perm_config *cfgs
         max_s = std::max(max_s, (double)P[r].max_ns * 1e-9);
     }
     const int threads = 32 * (warps + 1);
-    int ctas = 0;
-    if (rc == PERM_OK && perm::batch_grid(threads, smem, &ctas) != cudaSuccess) rc = PERM_EUNSUPPORTED;
+    // every CTA of the grid must be resident at once: walks wait (boundedly) on
+    // copies that other CTAs' walks hand over
+    int resident = 0;
+    if (rc == PERM_OK && (perm::batch_grid(threads, smem, &resident) != cudaSuccess || resident < grid))
+        rc = PERM_EUNSUPPORTED;
     if (rc == PERM_OK && cudaMalloc((void **)&b->d_runs, sizeof(perm::RunDev) * R) != cudaSuccess) rc = PERM_ENOMEM;
     if (rc == PERM_OK && cudaMalloc((void **)&b->d_ctl, sizeof(int) * (3 * (size_t)R + 1)) != cudaSuccess) rc = PERM_ENOMEM;
     if (rc == PERM_OK &&
@@ -210,7 +213,6 @@ int perm_batch_create_persistent(perm_batch_handle *out, const perm_config *cfgs
         batch_free(b);
         return rc;
     }
-    (void)ctas;
     *out = b;
     return PERM_OK;
 }
