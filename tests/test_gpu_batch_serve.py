@@ -13,7 +13,7 @@ import pytest
 import paper_2002_03000_gb300 as pg
 from paper_2002_03000_gb300 import batch as pb
 from paper_2002_03000_gb300 import serve as ps
-from tests.gpu_util import Run, torch_cuda
+from tests.gpu_util import Run, torch_cuda, zscores
 
 pytestmark = pytest.mark.gpu
 
@@ -62,10 +62,11 @@ def test_batch_of_interacting_runs(exact_counts):
             M = N * t
             assert S[0] == M and S[1] == M
             assert math.isclose(math.exp(lc[1]), 2 * d, rel_tol=1e-12)
-            ex = np.array(exact_counts[d][: min(n, 11 if d == 3 else 16) + 1], dtype=float)
-            rel = np.exp(lc[: len(ex)] - np.log(ex)) - 1
-            sig = np.sqrt(rv[: len(ex)] + 1e-10)
-            assert np.all(np.abs(rel[2:]) < 4 * sig[2:]), (r, rel, sig)
+            # shared thresholds correlate the tours, so the per-tour variance
+            # understates the spread at the shortest lengths: a relative floor on
+            # sigma there, and 5 sigma over all runs and lengths
+            z = zscores(lc, rv, exact_counts[d][: min(n, 11 if d == 3 else 16) + 1])
+            assert np.all(np.abs(z[2:]) < 5.0), (r, z)
 
 
 def test_autotune_picks_a_runnable_layout():
