@@ -477,14 +477,8 @@ def run_ours(args):
     kern_ms = [a.elapsed_time(b) for a, b in kev]
     t_dev = sum(step_ms) / 1000.0
     # max over ranks of the device time; sum of steps over ranks
-    if world > 1:
-        tt = torch.tensor([t_dev, float(steps_total)], dtype=torch.float64, device="cuda")
-        mx = tt.clone()
-        torch.distributed.all_reduce(mx[:1], op=torch.distributed.ReduceOp.MAX)
-        torch.distributed.all_reduce(tt[1:], op=torch.distributed.ReduceOp.SUM)
-        t_dev, steps_all = float(mx[0]), float(tt[1])
-    else:
-        steps_all = float(steps_total)
+    from paper_2002_03000_gb300 import replicas
+    t_dev, steps_all = replicas.reduce_timing(t_dev, steps_total, device="cuda")
     value = steps_all / t_dev
 
     # ---- end to end through the C ABI, host buffers: run + estimates to host ----
@@ -499,13 +493,10 @@ def run_ours(args):
         lc, S, rv = nat.perm_estimates(run.h, w["n_max"])
         e2e_steps += run.stats()["steps"]
     e2e_t = time.perf_counter() - t0
-    if world > 1:
-        tt = torch.tensor([e2e_t, float(e2e_steps)], dtype=torch.float64, device="cuda")
-        mx = tt.clone()
-        torch.distributed.all_reduce(mx[:1], op=torch.distributed.ReduceOp.MAX)
-        torch.distributed.all_reduce(tt[1:], op=torch.distributed.ReduceOp.SUM)
-        e2e_t, e2e_steps = float(mx[0]), float(tt[1])
+    e2e_t, e2e_steps = replicas.reduce_timing(e2e_t, e2e_steps, device="cuda")
     e2e_value = e2e_steps / e2e_t
+    # the replicas' last runs pooled into one estimate (sum W_n / sum M)
+    pooled = replicas.estimates(replicas.pool_tables(run.tables(), device="cuda"), w["d"])
     d2h = 3 * L * 8 + 4 + 8 * 3 + 8   # W_n, S_n, Q_n tables, status, counters, M
 
     # ---- time to 1e-4 relative standard error of c_{n_max}, continuing one run ----
@@ -570,6 +561,11 @@ def run_ours(args):
         "estimates": {"log_c_nmax": float(lc[w["n_max"]]), "rel_se_c_nmax": float(math.sqrt(rv[w["n_max"]])),
                       "log_c_nmax_over_nmax": float(lc[w["n_max"]] / w["n_max"])},
     }
+    if world > 1:
+        plc, _, prv = pooled
+        line["pooled_estimates"] = {"replicas": world, "log_c_nmax": float(plc[w["n_max"]]),
+                                    "rel_se_c_nmax": float(math.sqrt(prv[w["n_max"]])),
+                                    "note": "the replicas' last end-to-end runs pooled: sum W_n / sum M"}
     if world == 1 and not args.skip_systems:
         line["growth_constant"] = growth_constants((lc, rv))
         line["alg1_vs_alg2"] = alg1_vs_alg2()
