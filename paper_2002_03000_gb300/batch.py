@@ -21,19 +21,19 @@ class Batch:
     between runs as their tours run out)."""
 
     def __init__(self, configs, tours, n_streams=0, persistent=False):
-        self.configs = list(configs)
+        self.run_cfgs = list(configs)
         self.tours = [int(t) for t in tours]
         self.persistent = bool(persistent)
         if self.persistent:
-            self.b = nat.perm_batch_create_persistent(self.configs, self.tours)
+            self.b = nat.perm_batch_create_persistent(self.run_cfgs, self.tours)
         else:
-            self.b = nat.perm_batch_create(self.configs, self.tours, n_streams)
+            self.b = nat.perm_batch_create(self.run_cfgs, self.tours, n_streams)
 
     def run(self):
         nat.perm_batch_run(self.b)
 
     def estimates(self, r):
-        return nat.perm_batch_estimates(self.b, r, self.configs[r].n_max)
+        return nat.perm_batch_estimates(self.b, r, self.run_cfgs[r].n_max)
 
     def stats(self, r):
         return nat.perm_batch_stats(self.b, r)
