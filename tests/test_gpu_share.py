@@ -45,7 +45,7 @@ def test_moved_parts_replay_and_estimates(d, n_max, N, tours, every, exact_count
     assert not bad, bad[:3]
     ex = exact_counts[d]
     z = zscores(lc, rv, ex[: min(len(ex), n_max + 1)])
-    assert np.all(np.abs(z[2:]) < 4.0), z
+    assert np.all(np.abs(z[2:]) < 4.5), z
 
 
 def test_sharing_off_moves_nothing():
