@@ -8,7 +8,7 @@ point and grows the copy's subtree; the weights of that part still count for
 the tour that made the copy (its per-tour sum, and the tour finishes once
 all of its parts have).  The runs here start with most walks idle, so many
 copies move: every tour still finishes exactly once, the estimates stay
-unbiased (c_n within 4 sigma of the exact counts, S_0 = S_1 = M), and sampled
+unbiased (c_n within 4.5 sigma of the exact counts, S_0 = S_1 = M), and sampled
 nodes of moved parts (ordinal high word = part id) replay bit for bit in the
 oracle's growth step.
 """
