@@ -44,12 +44,29 @@ def bytes_per_step(d, f):
 KERNEL_SOURCES = ("perm_kernels.cu", "perm_kernels.cuh", "perm_device.cuh")
 
 
-def kernel_sources_sha256():
+def code_tokens(text):
+    """The code of a C++/CUDA source without its comments and with whitespace
+    runs collapsed, so that a changed comment does not count as a changed
+    kernel (the sources hold no string literal with a comment marker)."""
+    import re
+    text = re.sub(r"/\*.*?\*/", " ", text, flags=re.S)
+    text = re.sub(r"//[^\n]*", " ", text)
+    return " ".join(text.split())
+
+
+def kernel_sources_sha256(texts=None):
+    """SHA-256 over the code (comments dropped) of the growth kernel's sources;
+    texts: the sources' contents in KERNEL_SOURCES order (default: the files)."""
     import hashlib
     h = hashlib.sha256()
-    for name in KERNEL_SOURCES:
-        with open(os.path.join(ROOT, "paper_2002_03000_gb300", "csrc", name), "rb") as f:
-            h.update(f.read())
+    if texts is None:
+        texts = []
+        for name in KERNEL_SOURCES:
+            with open(os.path.join(ROOT, "paper_2002_03000_gb300", "csrc", name), encoding="utf-8") as f:
+                texts.append(f.read())
+    for t in texts:
+        h.update(code_tokens(t).encode("utf-8"))
+        h.update(b"\0")
     return h.hexdigest()
 
 

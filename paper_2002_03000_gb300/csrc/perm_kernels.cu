@@ -9,15 +9,20 @@
 // the tree of copies made by enrichment (Sec. 2).
 //
 // Threshold sources for Algorithm 2 (one shared table W, Fig. 1):
-//  - snapshot: every CTA accumulates W_n, S_n and Q_n into shared-memory
-//    deltas; one extra warp per CTA flushes them to the global table every
-//    refresh period and reloads a shared-memory copy of [W_n] = W_n/M.  The
-//    nodes read that copy (a stale but fixed threshold keeps the estimator
-//    unbiased: enrichment and pruning conserve the expected weight for any r).
+//  - snapshot: every CTA accumulates W_n and S_n into shared-memory deltas; one
+//    extra warp per CTA flushes them to the global table every refresh period
+//    and reloads a shared-memory copy of [W_n] = W_n/M.  The nodes read that
+//    copy (a stale but fixed threshold keeps the estimator unbiased: enrichment
+//    and pruning conserve the expected weight for any r).  Walks with no tour to
+//    start grow waiting copies of other walks' tours (shared copies).
 //  - fresh: every node adds its weight to the global table with an atomic that
 //    returns the previous sum, and uses it at once (sequential flatPERM exactly
 //    when one walk runs).
-// Algorithm 1 (private tables) always uses the fresh form on its own rows.
+// Algorithm 1 (private tables) always uses the fresh form on its own rows.  The
+// per-tour sums X_n go to a global row per walk and, squared, into Q_n when the
+// tour ends.  With cut-offs set (original PERM, Sec. 2) r comes from the
+// cut-offs instead of the table.  The batch kernel at the end grows many runs
+// in one persistent launch with the same per-run body.
 #include <cstdio>
 
 #include "perm_device.cuh"
