@@ -379,7 +379,8 @@ __device__ __forceinline__ void grow_run(const RunDev &P, unsigned char *smem, c
             break;
         }
         // in a batch launch a failed run stops at once, so that its CTAs move on
-        if (bl != nullptr && (iter & 255) == 0 && *(volatile int *)P.status != 0) break;
+        // (the whole warp leaves together: one lane's read decides)
+        if (bl != nullptr && (iter & 255) == 0 && __shfl_sync(kFull, *(volatile int *)P.status, 0) != 0) break;
         // ---------------- tour tickets ----------------
         if (state == kNeed && xbusy && *(volatile unsigned int *)(P.outst + sidx) == kRowFree) xbusy = false;
         const bool want_t = state == kNeed && !xbusy && !exhausted;
@@ -484,7 +485,9 @@ __device__ __forceinline__ void grow_run(const RunDev &P, unsigned char *smem, c
             // ---------------- shared copies: idle walks take queued ones ----------------
             const bool idle = state == kNeed && (waiting || xbusy || exhausted);
             const unsigned hm = __ballot_sync(kFull, idle);
-            if (hm && *(volatile int *)&head->queued > 0) {
+            // one lane's read of the queue length decides for the warp (the block
+            // below exchanges values across all lanes)
+            if (hm && __shfl_sync(kFull, *(volatile int *)&head->queued, 0) > 0) {
                 const int leader = __ffs(hm) - 1;
                 unsigned long long base = 0ull, take = 0ull;
                 if (lane == leader) {
