@@ -205,8 +205,12 @@ def batched_vs_plain(tours):
                        "sequences log-uniform in [256,8192] (PCG64 seed 1), %d tours per sequence" % tours,
            "tours_per_seq": tours}
     forms = {}
-    for form in ("streams", "persistent"):
-        b = pb.Batch(cfgs, [tours] * len(runs), persistent=(form == "persistent"))
+    for form in ("persistent", "streams"):
+        # the streams form can stall on a start-up tree that its run's few CTAs grow
+        # alone; a 60 s bound (3x its usual time) keeps that from holding the bench
+        cf = cfgs if form == "persistent" else [
+            pb.make_config(d, n, N, 1, run_id=i, max_seconds=60.0) for i, (d, n, N) in enumerate(runs)]
+        b = pb.Batch(cf, [tours] * len(runs), persistent=(form == "persistent"))
         try:
             b.run()                                   # warm-up (and first replay)
             torch.cuda.synchronize()
