@@ -51,3 +51,24 @@ def test_argument_checks_need_no_device(lib):
     assert L.perm_run(None, 5) == _native.PERM_EINVAL
     assert L.perm_debug_step(2, 600, 1, *([None] * 8), 0, 0, *([None] * 4), None) == _native.PERM_EINVAL
     L.perm_destroy(None)   # NULL-safe
+
+
+def test_cutoff_and_batch_argument_checks_need_no_device(lib):
+    L = _native.load()
+    b = ctypes.c_void_p()
+    # original PERM cut-offs: a NULL handle is rejected
+    assert L.perm_set_cutoffs(None, None, None, 2, 2.0) == _native.PERM_EINVAL
+    # batches: no runs, or a negative tour count, are rejected before any device call
+    cfg = (_native.perm_config * 1)(_native.perm_config_init(2, 16, 4, 1))
+    tours = (ctypes.c_int64 * 1)(-1)
+    assert L.perm_batch_create(ctypes.byref(b), cfg, tours, 0, 0) == _native.PERM_EINVAL
+    assert L.perm_batch_create(ctypes.byref(b), cfg, tours, 1, 0) == _native.PERM_EINVAL
+    assert L.perm_batch_create_persistent(ctypes.byref(b), cfg, tours, 0) == _native.PERM_EINVAL
+    assert L.perm_batch_create_persistent(ctypes.byref(b), cfg, tours, 1) == _native.PERM_EINVAL
+    # the persistent form takes Algorithm-2 snapshot runs only
+    alg1 = _native.perm_config_init(2, 16, 4, 1)
+    alg1.alg = _native.PERM_ALG1
+    cfg1 = (_native.perm_config * 1)(alg1)
+    ok_tours = (ctypes.c_int64 * 1)(2)
+    assert L.perm_batch_create_persistent(ctypes.byref(b), cfg1, ok_tours, 1) == _native.PERM_EUNSUPPORTED
+    L.perm_batch_destroy(None)   # NULL-safe
