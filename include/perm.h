@@ -125,6 +125,22 @@ int perm_set_stream(perm_handle h, void *stream);
  * back to flatPERM.  PERM_EINVAL on a bad argument. */
 int perm_set_cutoffs(perm_handle h, const double *T_hi, const double *t_lo, int copies, double q);
 
+/* Checkpoint and resume (no counterpart in the paper).  perm_save waits for the
+ * handle's stream, then writes the run's state at that tour boundary to `path`:
+ * the configuration, the tables W_n, S_n, Q_n (and the eq. 5 sums when
+ * observables are on), the tour counters (M, tours per sequence), the cut-offs
+ * if set, and the statistics.  The file is written beside `path` and renamed,
+ * so a failure leaves no partial checkpoint.  A run whose status is an error is
+ * not saved (that code is returned).  perm_load creates a new handle from such
+ * a file (same library build; any GB300): runs on it continue where the saved
+ * run stopped, with the same random streams, so a run with sharing off (fresh
+ * thresholds, or share_copies = -1) continues exactly as if it had not been
+ * interrupted.  PERM_EINVAL for a file that is not a complete checkpoint. */
+int perm_save(perm_handle h, const char *path);
+int perm_load(perm_handle *out, const char *path);
+/* The configuration a handle runs with (defaults filled in), e.g. of a loaded one. */
+int perm_get_config(perm_handle h, perm_config *out);
+
 /* Grow tours_per_seq more tours of every sequence (cumulative: repeated calls
  * continue the same tables, tour counters and random streams).  Queues one
  * persistent kernel launch and returns without waiting unless `sync` is set

@@ -34,6 +34,20 @@ class Run:
         self.d, self.n_max, self.n_seq, self.alg = d, n_max, n_seq, alg
         self.h = _native.perm_create_ex(cfg)
 
+    def save(self, path):
+        """Checkpoint at the current tour boundary (see perm_save)."""
+        _native.perm_save(self.h, path)
+
+    @classmethod
+    def load(cls, path):
+        """A Run continuing the checkpoint at `path` (see perm_load)."""
+        self = cls.__new__(cls)
+        self.h = None
+        self.h = _native.perm_load(path)
+        cfg = _native.perm_get_config(self.h)
+        self.d, self.n_max, self.n_seq, self.alg = cfg.d, cfg.n_max, cfg.n_seq, cfg.alg
+        return self
+
     def set_cutoffs(self, T_hi, t_lo, copies=2, q=2.0):
         """Original PERM (Sec. 2) from now on: enrich into `copies` copies above
         T_hi[n], prune with probability 1 - 1/q below t_lo[n] (both n_max+1

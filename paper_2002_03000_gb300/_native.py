@@ -33,7 +33,7 @@ EXPORTS = (
     "perm_config_init", "perm_create", "perm_create_ex", "perm_set_stream", "perm_run", "perm_reset",
     "perm_run_sync", "perm_estimates", "perm_tables", "perm_stats", "perm_trace_enable",
     "perm_trace_read", "perm_destroy", "perm_strerror", "perm_debug_step", "perm_debug_philox",
-    "perm_run_static", "perm_set_cutoffs", "perm_batch_create", "perm_batch_create_persistent", "perm_batch_run", "perm_batch_size",
+    "perm_run_static", "perm_set_cutoffs", "perm_save", "perm_load", "perm_get_config", "perm_batch_create", "perm_batch_create_persistent", "perm_batch_run", "perm_batch_size",
     "perm_batch_estimates", "perm_batch_stats", "perm_batch_destroy", "perm_autotune",
     "perm_observable_r2",
 )
@@ -111,6 +111,9 @@ def load(path: str = LIB_PATH):
     L.perm_run_static.argtypes = [C.POINTER(perm_config), i64, vp, vp, vp, C.POINTER(i64), vp]
     L.perm_batch_create.argtypes = [hp, C.POINTER(perm_config), C.POINTER(i64), C.c_int, C.c_int]
     L.perm_set_cutoffs.argtypes = [vp, dp, dp, C.c_int, C.c_double]
+    L.perm_save.argtypes = [vp, C.c_char_p]
+    L.perm_load.argtypes = [hp, C.c_char_p]
+    L.perm_get_config.argtypes = [vp, C.POINTER(perm_config)]
     L.perm_batch_create_persistent.argtypes = [hp, C.POINTER(perm_config), C.POINTER(i64), C.c_int]
     L.perm_batch_run.argtypes = [vp]
     L.perm_batch_size.argtypes = [vp]
@@ -252,6 +255,24 @@ def perm_batch_create(cfgs, tours, n_streams=0):
     b = C.c_void_p()
     _check(load().perm_batch_create(C.byref(b), arr, t, R, n_streams), "perm_batch_create")
     return b
+
+
+def perm_save(h, path):
+    """Checkpoint the run at its current tour boundary."""
+    _check(load().perm_save(h, os.fsencode(path)), "perm_save")
+
+
+def perm_load(path):
+    """A new handle continuing a checkpointed run."""
+    h = C.c_void_p()
+    _check(load().perm_load(C.byref(h), os.fsencode(path)), "perm_load")
+    return h
+
+
+def perm_get_config(h):
+    cfg = perm_config()
+    _check(load().perm_get_config(h, C.byref(cfg)), "perm_get_config")
+    return cfg
 
 
 def perm_set_cutoffs(h, T_hi, t_lo, copies=2, q=2.0):

@@ -9,6 +9,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <string>
 #include <vector>
 
 #include <cuda_runtime.h>
@@ -694,3 +695,152 @@ int member_reset(perm_handle h) {
 }
 
 }  // namespace perm
+
+// ---------------------------------------------------------------------------
+// Checkpoint and resume at a tour boundary.  Between launches every tour of the
+// handle has ended: the per-walk tour sums are zero, the stacks are empty and
+// no copy waits in the donation ring, so the run's state is its tables, its
+// tour counters and its statistics.  The random streams are counter-based
+// (sequence, tour, node), so a resumed run draws what the uninterrupted run
+// would have drawn.
+// ---------------------------------------------------------------------------
+namespace {
+
+constexpr char kCkptMagic[8] = {'P', 'E', 'R', 'M', 'C', 'K', 'P', '1'};
+constexpr uint32_t kCkptVersion = 1;
+
+struct CkptHeader {
+    char magic[8];
+    uint32_t version;
+    uint32_t header_bytes;
+    perm_config cfg;               // as the handle holds it (defaults filled in)
+    int64_t tour_limit, seq_target;
+    int32_t ntab, has_rn, has_cut, pad0;
+    float r_hi, r_lo;
+    uint64_t steps, max_stack, copies, refreshes, iterations, finished;
+};
+
+// Bytes of the arrays after the header, or 0 when the sizes make no sense.
+uint64_t ckpt_payload(const CkptHeader &hd) {
+    const uint64_t L = (uint64_t)hd.cfg.n_max + 1;
+    if (hd.cfg.n_max < 1 || hd.cfg.n_seq < 1 || hd.cfg.n_max > (1 << 20)) return 0;
+    const uint64_t ntab = hd.cfg.alg == PERM_ALG1 ? (uint64_t)hd.cfg.n_seq : 1;
+    if ((uint64_t)hd.ntab != ntab || L * ntab > (1ull << 34)) return 0;
+    const uint64_t cnt = L * ntab;
+    return cnt * 8 * (3 + (hd.has_rn ? 1 : 0)) + (uint64_t)hd.cfg.n_seq * 8 + (hd.has_cut ? L * 16 : 0);
+}
+
+}  // namespace
+
+extern "C" {
+
+int perm_save(perm_handle h, const char *path) {
+    if (!h || !path) return PERM_EINVAL;
+    const int st = sync_status(h);
+    if (st != PERM_OK) return st < 0 ? st : PERM_EINVAL;     // a failed run is not saved
+    CkptHeader hd;
+    std::memset(&hd, 0, sizeof(hd));
+    std::memcpy(hd.magic, kCkptMagic, 8);
+    hd.version = kCkptVersion;
+    hd.header_bytes = (uint32_t)sizeof(CkptHeader);
+    hd.cfg = h->cfg;
+    hd.tour_limit = h->tour_limit;
+    hd.seq_target = h->seq_target;
+    hd.ntab = h->ntab;
+    hd.has_rn = h->Rn != nullptr;
+    hd.has_cut = h->cut != nullptr;
+    hd.r_hi = h->r_hi;
+    hd.r_lo = h->r_lo;
+    const size_t L = (size_t)h->cfg.n_max + 1, cnt = L * h->ntab;
+    std::vector<double> W(cnt), Q(cnt), R(hd.has_rn ? cnt : 0);
+    std::vector<unsigned long long> S(cnt), sM(h->cfg.n_seq);
+    std::vector<double2> cut(hd.has_cut ? L : 0);
+    cudaError_t e = copy_out(h, W.data(), h->Wn, cnt * 8);
+    if (e == cudaSuccess) e = copy_out(h, Q.data(), h->Qn, cnt * 8);
+    if (e == cudaSuccess) e = copy_out(h, S.data(), h->Sn, cnt * 8);
+    if (e == cudaSuccess && hd.has_rn) e = copy_out(h, R.data(), h->Rn, cnt * 8);
+    if (e == cudaSuccess) e = copy_out(h, sM.data(), h->seq_M, sM.size() * 8);
+    if (e == cudaSuccess && hd.has_cut) e = copy_out(h, cut.data(), h->cut, L * sizeof(double2));
+    unsigned long long *cnts[6] = {h->steps, h->max_stack, h->copies, h->refreshes, h->iterations, h->finished};
+    uint64_t *dst[6] = {&hd.steps, &hd.max_stack, &hd.copies, &hd.refreshes, &hd.iterations, &hd.finished};
+    for (int i = 0; e == cudaSuccess && i < 6; ++i) e = copy_out(h, dst[i], cnts[i], 8);
+    if (e != cudaSuccess) return to_code(e);
+    // write beside the target, then rename: a crash never leaves half a checkpoint
+    const std::string tmp = std::string(path) + ".tmp";
+    FILE *f = std::fopen(tmp.c_str(), "wb");
+    if (!f) return PERM_EINVAL;
+    bool ok = std::fwrite(&hd, sizeof(hd), 1, f) == 1;
+    ok = ok && std::fwrite(W.data(), 8, cnt, f) == cnt;
+    ok = ok && std::fwrite(Q.data(), 8, cnt, f) == cnt;
+    ok = ok && std::fwrite(S.data(), 8, cnt, f) == cnt;
+    if (hd.has_rn) ok = ok && std::fwrite(R.data(), 8, cnt, f) == cnt;
+    ok = ok && std::fwrite(sM.data(), 8, sM.size(), f) == sM.size();
+    if (hd.has_cut) ok = ok && std::fwrite(cut.data(), sizeof(double2), L, f) == L;
+    ok = (std::fclose(f) == 0) && ok;
+    if (!ok || std::rename(tmp.c_str(), path) != 0) {
+        std::remove(tmp.c_str());
+        return PERM_EINVAL;
+    }
+    return PERM_OK;
+}
+
+int perm_get_config(perm_handle h, perm_config *out) {
+    if (!h || !out) return PERM_EINVAL;
+    *out = h->cfg;
+    return PERM_OK;
+}
+
+int perm_load(perm_handle *out, const char *path) {
+    if (!out || !path) return PERM_EINVAL;
+    *out = nullptr;
+    FILE *f = std::fopen(path, "rb");
+    if (!f) return PERM_EINVAL;
+    CkptHeader hd;
+    bool ok = std::fread(&hd, sizeof(hd), 1, f) == 1 && std::memcmp(hd.magic, kCkptMagic, 8) == 0 &&
+              hd.version == kCkptVersion && hd.header_bytes == (uint32_t)sizeof(CkptHeader);
+    const uint64_t payload = ok ? ckpt_payload(hd) : 0;
+    ok = ok && payload > 0;
+    std::vector<unsigned char> body(ok ? (size_t)payload : 0);
+    ok = ok && std::fread(body.data(), 1, body.size(), f) == body.size();
+    ok = ok && std::fgetc(f) == EOF;                        // nothing after the arrays
+    std::fclose(f);
+    if (!ok) return PERM_EINVAL;
+    perm_handle h = nullptr;
+    int rc = perm_create_ex(&h, &hd.cfg);
+    if (rc != PERM_OK) return rc;
+    if (hd.has_rn != (h->Rn != nullptr)) { perm_destroy(h); return PERM_EINVAL; }
+    const size_t L = (size_t)hd.cfg.n_max + 1, cnt = L * (size_t)hd.ntab;
+    const unsigned char *p = body.data();
+    auto put = [&](void *dev, size_t bytes) {
+        cudaError_t e = cudaMemcpyAsync(dev, p, bytes, cudaMemcpyHostToDevice, h->stream);
+        p += bytes;
+        return e;
+    };
+    cudaError_t e = put(h->Wn, cnt * 8);
+    if (e == cudaSuccess) e = put(h->Qn, cnt * 8);
+    if (e == cudaSuccess) e = put(h->Sn, cnt * 8);
+    if (e == cudaSuccess && hd.has_rn) e = put(h->Rn, cnt * 8);
+    if (e == cudaSuccess) e = put(h->seq_M, (size_t)hd.cfg.n_seq * 8);
+    if (e == cudaSuccess && hd.has_cut) {
+        rc = dalloc(h, &h->cut, L);
+        if (rc != PERM_OK) { perm_destroy(h); return rc; }
+        e = put(h->cut, L * sizeof(double2));
+        h->r_hi = hd.r_hi;
+        h->r_lo = hd.r_lo;
+    }
+    // the tour counter: Alg. 2 hands out tickets from the tours started so far
+    const unsigned long long tickets = hd.cfg.alg == PERM_ALG2 ? (unsigned long long)hd.tour_limit : 0ull;
+    const uint64_t vals[7] = {hd.steps, hd.max_stack, hd.copies, hd.refreshes, hd.iterations, hd.finished, tickets};
+    unsigned long long *dev[7] = {h->steps, h->max_stack, h->copies, h->refreshes, h->iterations, h->finished,
+                                  h->tickets};
+    for (int i = 0; e == cudaSuccess && i < 7; ++i)
+        e = cudaMemcpyAsync(dev[i], &vals[i], 8, cudaMemcpyHostToDevice, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) { perm_destroy(h); return to_code(e); }
+    h->tour_limit = hd.tour_limit;
+    h->seq_target = hd.seq_target;
+    *out = h;
+    return PERM_OK;
+}
+
+}  // extern "C"

@@ -72,3 +72,15 @@ def test_cutoff_and_batch_argument_checks_need_no_device(lib):
     ok_tours = (ctypes.c_int64 * 1)(2)
     assert L.perm_batch_create_persistent(ctypes.byref(b), cfg1, ok_tours, 1) == _native.PERM_EUNSUPPORTED
     L.perm_batch_destroy(None)   # NULL-safe
+
+
+def test_checkpoint_files_are_checked_before_any_device_call(lib, tmp_path):
+    L = _native.load()
+    h = ctypes.c_void_p()
+    assert L.perm_save(None, b"x") == _native.PERM_EINVAL
+    assert L.perm_load(ctypes.byref(h), str(tmp_path / "missing.ckpt").encode()) == _native.PERM_EINVAL
+    bad = tmp_path / "bad.ckpt"
+    bad.write_bytes(b"not a checkpoint" * 64)
+    assert L.perm_load(ctypes.byref(h), str(bad).encode()) == _native.PERM_EINVAL
+    assert not h.value
+    assert L.perm_get_config(None, None) == _native.PERM_EINVAL
