@@ -189,8 +189,8 @@ __device__ __forceinline__ int select_slot(const int (&eslot)[2 * D], int dir) {
 // What lets a CTA leave a run before every tour of the run has finished: in a
 // batch launch, another run still has walks to grant and tours to start
 // (runs_open > 0).  The first walk to find a run's tickets exhausted marks it
-// closed (bit 0 of its flag; bit 1: all its walks granted); the first mark takes
-// the run off runs_open.  Bit 2 of the flag says that no tour of the run has
+// closed (bit 0 of its flag; bit 1: all its walks granted); the first of those two
+// marks takes the run off runs_open.  Bit 2 of the flag says that no tour of the run has
 // finished for a while (its CTAs' refreshers set and clear it): such a run
 // draws helper CTAs before other unfinished runs do.
 struct BatchLeave {
@@ -441,7 +441,7 @@ __device__ __forceinline__ void grow_run(const RunDev &P, unsigned char *smem, c
                     if ((long long)g >= limit) {
                         if (P.share) exhausted = true;   // idle: may still take shared copies
                         else state = kDone;
-                        if (bl != nullptr && atomicOr(bl->closed + P.run_index, 1) == 0)
+                        if (bl != nullptr && (atomicOr(bl->closed + P.run_index, 1) & 3) == 0)
                             atomicSub(bl->runs_open, 1);
                     } else {
                         seq = (uint32_t)(g % (unsigned long long)P.n_seq);
@@ -970,7 +970,7 @@ __device__ int pick_run(const BatchDev &B, int &walks, bool &helper) {
             if (k <= 0) break;
             if (atomicCAS(B.granted + best, g, g + k) == g) {
                 walks = k;
-                if (g + k >= Q.n_seq && atomicOr(B.closed + best, 2) == 0) atomicSub(B.runs_open, 1);
+                if (g + k >= Q.n_seq && (atomicOr(B.closed + best, 2) & 3) == 0) atomicSub(B.runs_open, 1);
                 break;
             }
         }
