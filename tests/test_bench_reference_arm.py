@@ -24,3 +24,15 @@ def test_reference_arm_prints_one_json_line():
     assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == rec["value"] and cb["sample"]
     assert rec["e2e"] == {"value": rec["value"], "unit": rec["unit"], "h2d_bytes_per_step": 0,
                           "d2h_bytes_per_step": 0}
+
+
+def test_kernel_hash_ignores_comments_only():
+    """The hash that keeps the measured DRAM traffic tied to the kernel it was
+    measured on changes with the code and not with comments or spacing."""
+    sys.path.insert(0, ROOT)
+    import bench
+    a = "int f(int x) {  // one\n  return x + 1; /* two\n lines */ }\n"
+    b = "int f(int x) {\n  return x + 1;   }  // other words\n"
+    c = "int f(int x) { return x + 2; }\n"
+    assert bench.kernel_sources_sha256([a]) == bench.kernel_sources_sha256([b])
+    assert bench.kernel_sources_sha256([a]) != bench.kernel_sources_sha256([c])
