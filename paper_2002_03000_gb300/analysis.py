@@ -57,3 +57,32 @@ def t_m(log_cn, log_best):
     best = np.asarray(log_best, dtype=float)
     est = np.asarray(log_cn, dtype=float)[: len(best)]
     return float(np.mean(np.abs(best[1:] - est[1:])))
+
+
+def alg1_combine(tables, d, mode="arithmetic"):
+    """log c_n of an Algorithm-1 run from its per-sequence raw tables (the dict
+    Run.tables() returns: W with one row of n_max+1 per sequence at the stored
+    scale, M with each sequence's tours).
+
+    arithmetic: the displayed estimator of Sec. 3, log of the mean over sequences
+    of W_s/M_s (what perm_estimates returns);
+    geometric: the mean over sequences of log(W_s/M_s), the combination Sec. 4
+    uses for Algorithm 1's best estimate of log c_10000.  A length some sequence
+    never reached gives -inf there.  By the inequality of arithmetic and geometric
+    means the geometric form is never above the arithmetic one."""
+    import math
+    from .replicas import scale_exp
+    M = np.asarray(tables["M"], dtype=float).reshape(-1)
+    N = M.size
+    W = np.asarray(tables["W"], dtype=float).reshape(N, -1)
+    if np.any(M < 1):
+        raise ValueError("every sequence needs a tour")
+    c = W / M[:, None]
+    L = W.shape[1]
+    shift = np.array([scale_exp(d, n) for n in range(L)], dtype=float) * math.log(2.0)
+    with np.errstate(divide="ignore"):
+        if mode == "arithmetic":
+            return np.log(c.mean(axis=0)) + shift
+        if mode == "geometric":
+            return np.log(c).mean(axis=0) + shift
+    raise ValueError("mode is 'arithmetic' or 'geometric'")

@@ -11,6 +11,7 @@
 import math
 
 import numpy as np
+import pytest
 
 from paper_2002_03000_gb300.analysis import fit_eq15, t_m
 from tests.conftest import load_counts
@@ -47,3 +48,29 @@ def test_t_m_is_mean_abs_log_error_over_lengths_1_to_M():
     assert t_m(best, best) == 0.0
     est = best + np.array([5.0, 0.03, -0.06, 0.0])      # n = 0 does not count
     assert abs(t_m(est, best) - 0.03) < 1e-15
+
+
+def test_alg1_combinations_on_oracle_tables(exact_counts):
+    """Arithmetic: the oracle's own Algorithm-1 estimate.  Geometric: never above
+    it, equal for one sequence, and exact where every sequence is exact (n <= 3:
+    a sequential sequence's short lengths carry equal weights)."""
+    import math
+    from oracle import oracle as orc
+    from paper_2002_03000_gb300 import analysis
+    h = orc.Oracle(2, 14, 6, seed=4, alg=orc.ORC_ALG1)
+    h.run(40)
+    t = h.tables()
+    lo, _, _ = h.estimates()
+    ar = analysis.alg1_combine(t, 2, "arithmetic")
+    ge = analysis.alg1_combine(t, 2, "geometric")
+    assert np.allclose(ar, lo, rtol=1e-13, atol=1e-12)
+    assert np.all(ge <= ar + 1e-12)
+    for n in range(4):
+        assert math.isclose(math.exp(ge[n]), exact_counts[2][n], rel_tol=1e-12)
+    one = orc.Oracle(2, 10, 1, seed=4, alg=orc.ORC_ALG1)
+    one.run(30)
+    t1 = one.tables()
+    assert np.allclose(analysis.alg1_combine(t1, 2, "geometric"), analysis.alg1_combine(t1, 2, "arithmetic"),
+                       rtol=0, atol=1e-12)
+    with pytest.raises(ValueError):
+        analysis.alg1_combine(t, 2, "harmonic")
