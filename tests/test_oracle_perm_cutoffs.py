@@ -120,3 +120,59 @@ def test_cutoffs_reject_bad_arguments_and_switch_back():
     ref = orc.Oracle(2, 6, 1, seed=1)
     ref.run(3)
     assert np.array_equal(h.tables()["S"], ref.tables()["S"])
+
+
+def _rosenbluth_moments(d, n_max):
+    """By brute force over all n-step self-avoiding walks: their number, and the
+    sums of W and W^3, W(omega) being the Rosenbluth weight prod_{j<n} a_+(omega_j).
+    A Rosenbluth walk has probability 1/W, so E[W] = c_n, E[W^2] = sum W and
+    E[W^4] = sum W^3."""
+    steps = [tuple(1 if i == j // 2 and j % 2 == 0 else (-1 if i == j // 2 else 0) for i in range(d))
+             for j in range(2 * d)]
+    s0 = np.zeros(n_max + 1)
+    s1 = np.zeros(n_max + 1)
+    s3 = np.zeros(n_max + 1)
+
+    def rec(path, seen, w):
+        n = len(path) - 1
+        s0[n] += 1.0
+        s1[n] += w
+        s3[n] += w * w * w
+        if n == n_max:
+            return
+        end = path[-1]
+        free = [tuple(e + s for e, s in zip(end, st)) for st in steps]
+        free = [p for p in free if p not in seen]
+        for p in free:
+            seen.add(p)
+            path.append(p)
+            rec(path, seen, w * len(free))
+            path.pop()
+            seen.discard(p)
+
+    origin = tuple([0] * d)
+    rec([origin], {origin}, 1.0)
+    return s0, s1, s3
+
+
+@pytest.mark.parametrize("d,n_max,tours", [(2, 8, 6000), (3, 5, 6000)])
+def test_rosenbluth_second_moment_is_exact(d, n_max, tours):
+    """With no cut-off active every tour is one Rosenbluth walk, so the per-tour
+    sums X_t(n) are single weights and Q_n / M estimates E[W^2] = sum W exactly
+    (the brute-force sum over all walks); the mean square's own standard error
+    follows from E[W^4] = sum W^3."""
+    count, e2, e4 = _rosenbluth_moments(d, n_max)
+    h = orc.Oracle(d, n_max, 4, seed=61)
+    hi, lo = _cuts(d, n_max, lambda n: math.inf, lambda n: 0.0)
+    h.set_cutoffs(hi, lo, copies=2, q=2.0)
+    h.run(tours // 4)
+    t = h.tables()
+    M = float(t["M"][0])
+    for n in range(1, n_max + 1):
+        s = 2.0 ** orc.scale_exp(d, n)
+        mean_w2 = t["Q"][n] * s * s / M            # per-tour X^2 at the true scale
+        var_w2 = e4[n] - e2[n] ** 2                  # Var(W^2) = E[W^4] - E[W^2]^2
+        se = math.sqrt(max(var_w2, 0.0) / M)
+        assert abs(mean_w2 - e2[n]) <= 5.0 * se + 1e-9 * e2[n], (n, mean_w2, e2[n], se)
+        # the brute force counts the walks as the enumerator does
+        assert count[n] == float(orc.enumerate_cn(d, n_max)[n])
