@@ -43,6 +43,7 @@ MUTATIONS = {
     "cut-off comparison inverted": ("if (W > cuts->hi[n]) r = cuts->r_hi;", "if (W < cuts->hi[n]) r = cuts->r_hi;"),
     "cut-off survival probability q, not 1/q": ("h->cuts.r_lo = (float)(1.0 / q);", "h->cuts.r_lo = (float)q;"),
     "cut-offs applied at the empty walk": ("if (cuts && n > 0) {", "if (cuts) {"),
+    "tour sums carried into the next tour": ("h->X[k] = 0.0;", "h->X[k] *= 1.0;"),
 }
 
 
@@ -153,6 +154,20 @@ def _pins_hold(exact2):
         return False
     if not math.isclose(t["W"][2], S2 * 12.0 * (2.0 ** 32 / K) * 2.0 ** -orc.scale_exp(2, 2), rel_tol=1e-12):
         return False
+    # per-tour square sums against the exact Rosenbluth second moment (no cut-off
+    # active: one walk per tour, E[W^2] = sum over all walks of W)
+    from tests.test_oracle_perm_cutoffs import _rosenbluth_moments
+    count, e2, e4 = _rosenbluth_moments(2, 6)
+    h = orc.Oracle(2, 6, 4, seed=61)
+    h.set_cutoffs(np.full(7, np.inf), np.zeros(7), 2, 2.0)
+    h.run(1000)
+    t = h.tables()
+    M = float(t["M"][0])
+    for n in range(1, 7):
+        s2 = (2.0 ** orc.scale_exp(2, n)) ** 2
+        se = math.sqrt(max(e4[n] - e2[n] ** 2, 0.0) / M)
+        if abs(t["Q"][n] * s2 / M - e2[n]) > 5.0 * se + 1e-9 * e2[n]:
+            return False
     # the observable estimator (Sec. 1, eq. 5) against the exact mean |omega_n|^2
     c, r2 = orc.enumerate_r2(2, 10)
     h = orc.Oracle(2, 10, 6, seed=8)
