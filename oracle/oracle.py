@@ -26,13 +26,12 @@ def configure(L):
     L.orc_enumerate_r2.argtypes = [C.c_int, C.c_int, C.POINTER(C.c_int64), C.POINTER(C.c_int64)]
     L.orc_scale_exp.argtypes = [C.c_int, C.c_int]
     L.orc_ratio.argtypes = [C.c_int, C.c_double, C.c_double, C.c_int64]
-    L.orc_ratio.restype = C.c_float
+    L.orc_ratio.restype = C.c_double
     L.orc_step.argtypes = [
         C.c_int, C.c_int, C.c_int, C.POINTER(C.c_int32), C.c_double, C.c_double,
         C.c_int64, C.c_uint64, C.c_uint32, C.c_uint32, C.c_uint64, C.c_uint32,
-        C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_float),
         C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_double),
-        C.POINTER(C.c_uint64)]
+        C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_double)]
     L.orc_create.argtypes = [C.POINTER(C.c_void_p), C.c_int, C.c_int, C.c_int,
                              C.c_uint64, C.c_uint32, C.c_int]
     L.orc_run.argtypes = [C.c_void_p, C.c_int64]
@@ -89,25 +88,27 @@ def scale_exp(d: int, n: int) -> int:
     return lib().orc_scale_exp(d, n)
 
 
-def ratio(n: int, W: float, T: float, M: int) -> np.float32:
-    return np.float32(lib().orc_ratio(n, W, T, M))
+def ratio(n: int, W: float, Wsum: float, M: int) -> float:
+    """r = W / [W_n]^sample with [W_n]^sample = (Wsum + W) / M (Sec. 2, eq. 6)."""
+    return float(lib().orc_ratio(n, W, Wsum, M))
 
 
-def step(d, n_max, coords, W, T, M, ordinal, seq, tour, seed, run=0):
-    """Growth step of one node on a snapshot walk (coords: (n+1, d) int)."""
+def step(d, n_max, coords, W, Wsum, M, ordinal, seq, tour, seed, run=0):
+    """Growth step of one node on a snapshot walk (coords: (n+1, d) int).  W is
+    the node's weight, Wsum the sum of the weights recorded at its length before
+    it, M the tours started."""
     co = np.ascontiguousarray(coords, dtype=np.int32).reshape(-1)
     n = co.size // d - 1
-    a = C.c_int(0); mask = C.c_int(0); r = C.c_float(0); c = C.c_int(0)
+    a = C.c_int(0); mask = C.c_int(0); r = C.c_double(0); c = C.c_int(0)
     dirs = (C.c_int * 6)()
-    cw = C.c_double(0); K = C.c_uint64(0)
-    rc = lib().orc_step(d, n_max, n, _p(co, C.c_int32), W, T, M, ordinal, seq, tour,
+    cw = C.c_double(0)
+    rc = lib().orc_step(d, n_max, n, _p(co, C.c_int32), W, Wsum, M, ordinal, seq, tour,
                         seed, run, C.byref(a), C.byref(mask), C.byref(r), C.byref(c),
-                        dirs, C.byref(cw), C.byref(K))
+                        dirs, C.byref(cw))
     if rc < 0:
         raise ValueError("orc_step rejected the state: %d" % rc)
-    return dict(outcome=rc, a_plus=a.value, free_mask=mask.value, r=np.float32(r.value),
-                c=c.value, dirs=[dirs[i] for i in range(c.value)], child_w=cw.value,
-                survive_K=K.value)
+    return dict(outcome=rc, a_plus=a.value, free_mask=mask.value, r=r.value,
+                c=c.value, dirs=[dirs[i] for i in range(c.value)], child_w=cw.value)
 
 
 class Oracle:

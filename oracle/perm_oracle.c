@@ -21,9 +21,10 @@
  *    1-2), flatPERM ratio, enrichment and pruning (Sec. 2, eq. 6 and the
  *    paragraphs after it).  Pinned by exact c_0..c_3 in every run, by the
  *    counting theorem (Sec. 1, eq. 3: estimates within 4 sigma of the exact
- *    c_n from orc_enumerate), by weight conservation under enrichment, by the
- *    survival probability of pruning, and by the uniformity of the chosen
- *    directions.
+ *    c_n from orc_enumerate), by weight conservation under enrichment and
+ *    pruning, by the probabilities of the enrichment count and of survival,
+ *    by the uniformity of the chosen directions, and by r = 1 wherever the
+ *    own weight is the whole sum in the first tour.
  *  - original PERM with cut-offs (orc_set_cutoffs; Sec. 2, the paragraphs on
  *    T_k, t_k and q): pinned by its special cases -- no cut-off active is the
  *    Rosenbluth method (one sample per length per tour, exact c_2 and c_3 per
@@ -42,14 +43,13 @@
  *    weight is included in the running average (Sec. 2; Sec. 3, Alg. 2).
  *  - r is 1 at the empty walk, so every tour has exactly one node of length 0
  *    and one of length 1.
- *  - r is evaluated in single precision by the recipe in orc_ratio (the
- *    decision precision of the GPU kernel; mantissas are rounded to nearest,
- *    so that values within an ulp of each other give the same r except next
- *    to a rounding midpoint); weights stay in double precision.
+ *  - r is the paper's definition evaluated in double precision:
+ *    [W_n]^sample = (sum of the earlier weights at length n + W) / M and
+ *    r = W / [W_n]^sample; u0 = w0 2^-32 is exact in double precision, and
+ *    every comparison below is taken on these doubles.
  *  - Enriched copies take distinct steps, c is capped at a_+, each child has
- *    weight (W/c).a_+.  Survival after pruning has probability q = K/2^32 with
- *    K = ceil(r 2^32), and the survivor carries W/q (so the estimator stays
- *    exactly unbiased for the quantised r).
+ *    weight (W/c).a_+.  A survivor of pruning has its weight multiplied by
+ *    1/r (Sec. 2).
  *  - Random numbers: one Philox4x32-10 block per node, counter = (DFS ordinal
  *    of the node within its tour, 64 bit; tour index; sequence index), key =
  *    (low seed word XOR run id, high seed word).  Word 0 decides c (or
@@ -154,50 +154,15 @@ int orc_enumerate_r2(int d, int n, int64_t *c_out, int64_t *r2_out) {
 /* ------------------------------------------------------------------------- */
 int orc_scale_exp(int d, int n) { return d == 2 ? (11 * n) / 8 : (9 * n) / 4; }
 
-/* Mantissa of a positive normal double rounded to 24 bits (nearest, ties to
- * even) as a float in [1, 2), with the exponent adjusted for a carry. */
-static float mant24(uint64_t bits, int *ef) {
-    uint64_t frac = bits & 0xFFFFFFFFFFFFFull;
-    uint32_t keep = (uint32_t)(frac >> 29);
-    uint64_t rem = frac & 0x1FFFFFFFull, half = 0x10000000ull;
-    if (rem > half || (rem == half && (keep & 1u))) keep += 1u;
-    if (keep == (1u << 23)) { keep = 0u; *ef += 1; }
-    uint32_t fb = (127u << 23) | keep;
-    float f;
-    memcpy(&f, &fb, 4);
-    return f;
-}
-
-/* a/b for finite a >= 0, b > 0 in single precision: both mantissas are rounded
- * to 24 bits, divided in FP32 (round to nearest), and the exponent difference
- * (clamped to [-100, 100]) is applied exactly. */
-static float ratio_f32(double a, double b) {
-    uint64_t ab, bb;
-    memcpy(&ab, &a, 8);
-    memcpy(&bb, &b, 8);
-    int ea_f = (int)((ab >> 52) & 0x7FF), eb_f = (int)((bb >> 52) & 0x7FF);
-    if (ea_f == 0) return 0.0f;                        /* a zero (or subnormal) */
-    if (eb_f == 0) return 1.2676506e30f;               /* 2^100: b zero or subnormal */
-    float fa = mant24(ab, &ea_f), fb = mant24(bb, &eb_f);
-    float q = fa / fb;                                 /* in (0.5, 2) */
-    int e = ea_f - eb_f;
-    if (e > 100) e = 100;
-    if (e < -100) e = -100;
-    uint32_t p2_bits = (uint32_t)(e + 127) << 23;
-    float p2;
-    memcpy(&p2, &p2_bits, 4);
-    return q * p2;                                     /* exact power-of-two scaling */
-}
-
-/* r = W / [W_n]^sample with the own weight included (Sec. 2, eq. 6):
- * [W_n] = (sum of earlier weights + W) / M = T + W/M, so r = 1 / (T/W + 1/M). */
-float orc_ratio(int n, double W, double T, int64_t M) {
-    if (n == 0) return 1.0f;
-    float Mf = (float)M;
-    float invM = 1.0f / Mf;
-    float rho = ratio_f32(T, W);
-    float x = rho + invM;
-    return 1.0f / x;
+/* r = W / [W_n]^sample (Sec. 2, eq. 6), the running average of the weights
+ * of length n including the node's own weight W: [W_n]^sample =
+ * (Wsum + W) / M, where Wsum is the sum of the weights recorded at length n
+ * before this node and M the number of tours started.  The empty walk has
+ * r = 1 (every tour then visits lengths 0 and 1 exactly once). */
+double orc_ratio(int n, double W, double Wsum, int64_t M) {
+    if (n == 0) return 1.0;
+    double avg = (Wsum + W) / (double)M;
+    return W / avg;
 }
 
 /* ------------------------------------------------------------------------- */
@@ -256,30 +221,28 @@ static void add_step(int d, const int32_t *from, int j, int32_t *to) {
 /* ------------------------------------------------------------------------- */
 typedef struct {
     int a_plus, free_mask, c, dirs[6];
-    float r;
+    double r;
     double child_w;
-    uint64_t survive_K;
 } node_out;
 
 /* Original PERM (Sec. 2, the cut-offs T_k and t_k): a node of weight W above
- * T_n is enriched into `copies` copies of weight W/copies, one below t_n is
- * pruned with probability 1 - 1/q and otherwise carries q W.  Cut-offs are at
- * the stored weight scale.  Readings: the copies take distinct steps, at most
- * a_+ of them, each carrying W/c for the c made (as flatPERM's copies); the
- * survival probability is 1/q rounded to single precision, taken as the
- * integer threshold K = ceil((1/q) 2^32), and the survivor carries W 2^32/K;
- * the empty walk is neither enriched nor pruned. */
+ * T_n is enriched into `copies` copies, each with its weight divided by the
+ * number made; one below t_n is pruned with probability 1 - 1/q and otherwise
+ * has its weight multiplied by q.  Cut-offs are at the stored weight scale.
+ * Readings: the copies take distinct steps, at most a_+ of them (as flatPERM's
+ * copies); the survival test compares u0 with 1/q in double precision; the
+ * empty walk is neither enriched nor pruned. */
 typedef struct {
     const double *hi, *lo;   /* T_n and t_n, n = 0..n_max */
-    float r_hi, r_lo;        /* copies, and 1/q in single precision */
+    int copies;
+    double q;
 } perm_cuts;
 
 static int grow_node(int d, int n_max, int n, const int32_t *end, const occset *occ,
-                     double W, double T, int64_t M, uint64_t ordinal, uint32_t seq,
+                     double W, double Wsum, int64_t M, uint64_t ordinal, uint32_t seq,
                      uint32_t tour, uint64_t seed, uint32_t run, const perm_cuts *cuts,
                      node_out *o) {
-    o->a_plus = 0; o->free_mask = 0; o->c = 0; o->r = 0.0f; o->child_w = 0.0;
-    o->survive_K = 0;
+    o->a_plus = 0; o->free_mask = 0; o->c = 0; o->r = 0.0; o->child_w = 0.0;
     if (n == n_max) return ORC_LEAF_NMAX;                     /* walk complete */
 
     /* a_+: the free neighbours of the end-point (Sec. 1) */
@@ -295,38 +258,48 @@ static int grow_node(int d, int n_max, int n, const int32_t *end, const occset *
     o->a_plus = a;
     if (a == 0) return ORC_LEAF_TRAPPED;                       /* trapped: weight 0 beyond */
 
-    /* r (Sec. 2, eq. 6) and the node's random block */
-    float r = orc_ratio(n, W, T, M);
-    if (cuts && n > 0) {
-        /* original PERM: the same decision rules with r = copies (enrich: c copies
-         * of W/c), r = 1/q (prune: survive with probability 1/q, weight q W) or 1 */
-        if (W > cuts->hi[n]) r = cuts->r_hi;
-        else if (W < cuts->lo[n]) r = cuts->r_lo;
-        else r = 1.0f;
-    }
-    o->r = r;
+    /* the node's random block; u0 = w0 / 2^32 (exact in double precision) */
     uint32_t ctr[4] = {(uint32_t)ordinal, (uint32_t)(ordinal >> 32), tour, seq};
     uint32_t key[2] = {(uint32_t)seed ^ run, (uint32_t)(seed >> 32)};
     uint32_t w[4];
     orc_philox4x32_10(ctr, key, w);
+    double u0 = (double)w[0] * (1.0 / 4294967296.0);
 
     int c;
     double Wp;
-    if (r >= 1.0f) {
-        /* enrichment: p = ceil(r) - r; c = floor(r) with probability p, else ceil(r) */
-        float fl = floorf(r), ce = ceilf(r);
-        float p = ce - r;
-        uint64_t Kp = (uint64_t)ceilf(p * 4294967296.0f);   /* u0 < p  <=>  w0 < Kp */
-        float c_raw = ((uint64_t)w[0] < Kp) ? fl : ce;
-        c = (c_raw >= (float)a) ? a : (int)c_raw;             /* distinct steps: at most a_+ */
-        Wp = W / (double)c;                                   /* each copy carries W/c */
+    if (cuts && n > 0) {
+        /* original PERM (Sec. 2): enrich above T_n, prune below t_n, else one copy */
+        if (W > cuts->hi[n]) {
+            o->r = (double)cuts->copies;
+            c = cuts->copies < a ? cuts->copies : a;          /* distinct steps: at most a_+ */
+            Wp = W / (double)c;
+        } else if (W < cuts->lo[n]) {
+            o->r = 1.0 / cuts->q;
+            if (!(u0 < 1.0 / cuts->q)) return ORC_LEAF_PRUNED;   /* pruned w.p. 1 - 1/q */
+            c = 1;
+            Wp = W * cuts->q;                                     /* weight increased by q */
+        } else {
+            o->r = 1.0;
+            c = 1;
+            Wp = W;
+        }
     } else {
-        /* pruning: survive with probability q = K/2^32 (K = ceil(r 2^32)), weight W/q */
-        uint64_t K = (uint64_t)ceilf(r * 4294967296.0f);
-        o->survive_K = K;
-        if (!((uint64_t)w[0] < K)) return ORC_LEAF_PRUNED;
-        c = 1;
-        Wp = (W * 4294967296.0) / (double)K;
+        /* flatPERM (Sec. 2, eq. 6 and the two paragraphs after it) */
+        double r = orc_ratio(n, W, Wsum, M);
+        o->r = r;
+        if (r >= 1.0) {
+            /* enrichment: p = ceil(r) - r; c = floor(r) with probability p, else ceil(r) */
+            double fl = floor(r), ce = ceil(r);
+            double p = ce - r;
+            double c_raw = (u0 < p) ? fl : ce;
+            c = (c_raw >= (double)a) ? a : (int)c_raw;        /* distinct steps: at most a_+ */
+            Wp = W / (double)c;                               /* each copy carries W/c */
+        } else {
+            /* pruning with probability 1 - r; a survivor's weight times 1/r */
+            if (!(u0 < r)) return ORC_LEAF_PRUNED;
+            c = 1;
+            Wp = W * (1.0 / r);
+        }
     }
 
     /* c distinct directions: partial Fisher-Yates over the free list, draws from word 1 */
@@ -346,11 +319,11 @@ static int grow_node(int d, int n_max, int n, const int32_t *end, const occset *
     return ORC_CHILDREN;
 }
 
-int orc_step(int d, int n_max, int n, const int32_t *coords, double W, double T,
+int orc_step(int d, int n_max, int n, const int32_t *coords, double W, double Wsum,
              int64_t M, uint64_t ordinal, uint32_t seq, uint32_t tour,
              uint64_t seed, uint32_t run,
-             int *a_plus, int *free_mask, float *r, int *c, int *dirs,
-             double *child_w, uint64_t *survive_K) {
+             int *a_plus, int *free_mask, double *r, int *c, int *dirs,
+             double *child_w) {
     if ((d != 2 && d != 3) || n < 0 || n > n_max || n_max < 1 || !coords || M < 1)
         return ORC_EINVAL;
     /* the snapshot must be a self-avoiding walk from the origin */
@@ -368,7 +341,7 @@ int orc_step(int d, int n_max, int n, const int32_t *coords, double W, double T,
     occset occ;
     occ.d = d; occ.n_max = n_max; occ.box = NULL; occ.coords = coords; occ.n = n;
     node_out o;
-    int rc = grow_node(d, n_max, n, coords + (long)n * d, &occ, W, T, M, ordinal, seq,
+    int rc = grow_node(d, n_max, n, coords + (long)n * d, &occ, W, Wsum, M, ordinal, seq,
                        tour, seed, run, NULL, &o);
     if (a_plus) *a_plus = o.a_plus;
     if (free_mask) *free_mask = o.free_mask;
@@ -376,7 +349,6 @@ int orc_step(int d, int n_max, int n, const int32_t *coords, double W, double T,
     if (c) *c = o.c;
     if (dirs) for (int i = 0; i < o.c; ++i) dirs[i] = o.dirs[i];
     if (child_w) *child_w = o.child_w;
-    if (survive_K) *survive_K = o.survive_K;
     return rc;
 }
 
@@ -464,8 +436,9 @@ static int run_tour(orc_state *h, int tab, uint32_t seq, uint32_t tour, int64_t 
     h->occ.n = 0;
     occ_set(&h->occ, co, 1);
     for (;;) {
-        /* running average before this node, then accumulate the node (eq. 4) */
-        double T = Wn[n] / (double)M;
+        /* the sum of the earlier weights at this length, then accumulate the
+         * node (eq. 4) */
+        double Wsum = Wn[n];
         Wn[n] += W;
         Sn[n] += 1;
         h->X[n] += W;
@@ -479,7 +452,7 @@ static int run_tour(orc_state *h, int tab, uint32_t seq, uint32_t tour, int64_t 
         }
         h->steps += 1;
         node_out o;
-        int rc = grow_node(d, n_max, n, co + (long)n * d, &h->occ, W, T, M, ordinal,
+        int rc = grow_node(d, n_max, n, co + (long)n * d, &h->occ, W, Wsum, M, ordinal,
                            seq, tour, h->seed, h->run, h->cut_hi ? &h->cuts : NULL, &o);
         ordinal += 1;
         if (rc == ORC_CHILDREN) {
@@ -539,8 +512,8 @@ int orc_set_cutoffs(orc_state *h, const double *T_hi, const double *t_lo, int co
     memcpy(h->cut_lo, t_lo, L * sizeof(double));
     h->cuts.hi = h->cut_hi;
     h->cuts.lo = h->cut_lo;
-    h->cuts.r_hi = (float)copies;
-    h->cuts.r_lo = (float)(1.0 / q);
+    h->cuts.copies = copies;
+    h->cuts.q = q;
     return ORC_OK;
 }
 

@@ -43,22 +43,24 @@ int orc_enumerate_r2(int d, int n, int64_t *c_out, int64_t *r2_out);
 /* Power-of-two scale exponent E(n) of the stored weight (stored = W / 2^E(n)). */
 int orc_scale_exp(int d, int n);
 
-/* The ratio r of Sec. 2 in the kernel's FP32 recipe, from the node weight W,
- * the running average T = W_n(before this node)/M and M (own weight included
- * through the 1/M term).  n == 0 gives 1. */
-float orc_ratio(int n, double W, double T, int64_t M);
+/* The ratio r = W / [W_n]^sample of Sec. 2 (eq. 6) in double precision, from
+ * the node weight W, the sum Wsum of the weights recorded at length n before
+ * this node and the number M of tours started: [W_n]^sample = (Wsum + W)/M
+ * (own weight included).  n == 0 gives 1. */
+double orc_ratio(int n, double W, double Wsum, int64_t M);
 
 /* One node of the growth step on a snapshot state (walk coordinates given).
  * coords: (n+1)*d int32, site k at coords[k*d .. k*d+d-1], site 0 = origin.
+ * W: the node's weight; Wsum: the sum of the weights recorded at length n
+ * before it; M: tours started (both at the stored scale of length n).
  * Outputs: a_plus, free_mask (bit j = direction j free; order +x,-x,+y,-y,+z,-z),
- * r (FP32 bits), c (children), dirs[0..c-1], child weight (stored scale of
- * length n+1), survive_K (integer survival threshold, 0 if unused).
+ * r, c (children), dirs[0..c-1], child weight (stored scale of length n+1).
  * Returns the outcome code. */
-int orc_step(int d, int n_max, int n, const int32_t *coords, double W, double T,
+int orc_step(int d, int n_max, int n, const int32_t *coords, double W, double Wsum,
              int64_t M, uint64_t ordinal, uint32_t seq, uint32_t tour,
              uint64_t seed, uint32_t run,
-             int *a_plus, int *free_mask, float *r, int *c, int *dirs,
-             double *child_w, uint64_t *survive_K);
+             int *a_plus, int *free_mask, double *r, int *c, int *dirs,
+             double *child_w);
 
 typedef struct orc_state orc_state;
 
@@ -67,8 +69,8 @@ int orc_create(orc_state **out, int d, int n_max, int n_seq, uint64_t seed,
                uint32_t run, int alg);
 /* Original PERM with cut-offs (Sec. 2): from now on a node of length n >= 1 and
  * weight W > T_hi[n] is enriched into `copies` copies (distinct steps, at most
- * a_+, each W/c), one with W < t_lo[n] survives with probability 1/q (in
- * single precision) and then carries q W; the shared table no longer decides.
+ * a_+, each W/c), one with W < t_lo[n] survives with probability 1/q (u0 < 1/q
+ * in double precision) and then carries q W; the shared table no longer decides.
  * T_hi, t_lo: n_max+1 doubles at the stored scale, copied.  copies in
  * 1..2d, q >= 1.  Both NULL: back to flatPERM. */
 int orc_set_cutoffs(orc_state *h, const double *T_hi, const double *t_lo, int copies, double q);

@@ -46,16 +46,18 @@ def free_neighbours(walk):
 
 
 def random_state(rng, n):
-    """Scalar state of a node: weight W, running average T (before W), tours M,
-    DFS ordinal, sequence and tour indices."""
+    """Scalar state of a node: weight W, the sum Wsum of the weights recorded at
+    its length before it, tours M, DFS ordinal, sequence and tour indices."""
     W = float(10.0 ** rng.uniform(-3, 3))
-    # T spans both r < 1 and r > 1; sometimes exactly zero (first visit)
-    T = 0.0 if rng.random() < 0.05 else float(W * 10.0 ** rng.uniform(-1.5, 1.5))
     M = int(rng.integers(1, 1 << 20))
+    # Wsum is about M times a typical weight spread over three decades either
+    # side of W (so the node's weight is sometimes above and sometimes below
+    # the running average); sometimes exactly zero (first visit)
+    Wsum = 0.0 if rng.random() < 0.05 else float(W * M * 10.0 ** rng.uniform(-1.5, 1.5))
     ordinal = int(rng.integers(0, 1 << 40))
     seq = int(rng.integers(0, 1 << 16))
     tour = int(rng.integers(0, 1 << 20))
-    return dict(W=W, T=T, M=M, ordinal=ordinal, seq=seq, tour=tour)
+    return dict(W=W, Wsum=Wsum, M=M, ordinal=ordinal, seq=seq, tour=tour)
 
 
 def snapshot_batch(seed, d, n_max, count, n_lo=0):

@@ -20,12 +20,19 @@ SRC = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))),
 MUTATIONS = {
     "child weight misses a_+": ("o->child_w = ldexp(Wp * (double)a, -dE);",
                                 "o->child_w = ldexp(Wp, -dE);"),
-    "copies keep full weight": ("Wp = W / (double)c;", "Wp = W;"),
-    "survivor not reweighted": ("Wp = (W * 4294967296.0) / (double)K;", "Wp = W;"),
-    "own weight left out of r": ("float x = rho + invM;", "float x = rho;"),
-    "M off by one": ("double T = Wn[n] / (double)M;", "double T = Wn[n] / (double)(M + 1);"),
-    "rounding probability inverted": ("float c_raw = ((uint64_t)w[0] < Kp) ? fl : ce;",
-                                      "float c_raw = ((uint64_t)w[0] < Kp) ? ce : fl;"),
+    "copies keep full weight": ("Wp = W / (double)c;                               /* each copy",
+                                "Wp = W;                               /* each copy"),
+    "survivor not reweighted": ("Wp = W * (1.0 / r);", "Wp = W;"),
+    "survivor weight times r, not 1/r": ("Wp = W * (1.0 / r);", "Wp = W * r;"),
+    "own weight left out of r": ("double avg = (Wsum + W) / (double)M;", "double avg = Wsum / (double)M;"),
+    "M off by one": ("double avg = (Wsum + W) / (double)M;", "double avg = (Wsum + W) / (double)(M + 1);"),
+    "running average not divided by M": ("double avg = (Wsum + W) / (double)M;", "double avg = Wsum + W;"),
+    "ratio inverted": ("return W / avg;", "return avg / W;"),
+    "rounding probability inverted": ("double c_raw = (u0 < p) ? fl : ce;",
+                                      "double c_raw = (u0 < p) ? ce : fl;"),
+    "rounding probability from the fraction": ("double p = ce - r;", "double p = r - fl;"),
+    "survival with probability 1 - r": ("if (!(u0 < r)) return ORC_LEAF_PRUNED;",
+                                        "if (!(u0 < 1.0 - r)) return ORC_LEAF_PRUNED;"),
     "Fisher-Yates offset dropped": ("int j = i + (int)(prod >> 32);", "int j = (int)(prod >> 32);"),
     "backtrack leaves a site": ("for (int k = n; k > dp; --k) occ_set",
                                 "for (int k = n; k > dp + 1; --k) occ_set"),
@@ -34,14 +41,16 @@ MUTATIONS = {
     "scale step wrong": ("int dE = orc_scale_exp(d, n + 1) - orc_scale_exp(d, n);",
                          "int dE = orc_scale_exp(d, n + 1);"),
     "tour sum counts visits": ("h->X[n] += W;", "h->X[n] += 1.0;"),
-    "root ratio not forced": ("if (n == 0) return 1.0f;", "if (n < 0) return 1.0f;"),
+    "root ratio not forced": ("if (n == 0) return 1.0;", "if (n < 0) return 1.0;"),
     "Philox round permutation": ("uint32_t y0 = hi1 ^ x1 ^ k0;", "uint32_t y0 = hi0 ^ x1 ^ k0;"),
     "observable at the previous site": ("const int64_t x = co[(long)n * d + i];",
                                         "const int64_t x = co[(long)(n > 0 ? n - 1 : 0) * d + i];"),
     "observable not squared": ("r2 += x * x;", "r2 += x < 0 ? -x : x;"),
     "observable unweighted": ("Rn[n] += W * (double)r2;", "Rn[n] += (double)r2;"),
-    "cut-off comparison inverted": ("if (W > cuts->hi[n]) r = cuts->r_hi;", "if (W < cuts->hi[n]) r = cuts->r_hi;"),
-    "cut-off survival probability q, not 1/q": ("h->cuts.r_lo = (float)(1.0 / q);", "h->cuts.r_lo = (float)q;"),
+    "cut-off comparison inverted": ("if (W > cuts->hi[n]) {", "if (W < cuts->hi[n]) {"),
+    "cut-off survival probability q, not 1/q": ("if (!(u0 < 1.0 / cuts->q)) return ORC_LEAF_PRUNED;",
+                                                "if (!(u0 < cuts->q)) return ORC_LEAF_PRUNED;"),
+    "cut-off survivor not reweighted": ("Wp = W * cuts->q;", "Wp = W;"),
     "cut-offs applied at the empty walk": ("if (cuts && n > 0) {", "if (cuts) {"),
     "tour sums carried into the next tour": ("h->X[k] = 0.0;", "h->X[k] *= 1.0;"),
 }
@@ -54,7 +63,7 @@ def _pins_hold(exact2):
         return False
     # a_+ and free mask against an independent neighbour check
     for st in inputs.snapshot_batch(4, 2, 20, 60, n_lo=1):
-        out = orc.step(2, 30, st["walk"], st["W"], st["T"], st["M"], st["ordinal"],
+        out = orc.step(2, 30, st["walk"], st["W"], st["Wsum"], st["M"], st["ordinal"],
                        st["seq"], st["tour"], seed=5)
         free = inputs.free_neighbours(st["walk"])
         if out["free_mask"] != sum(1 << j for j in free):
@@ -74,18 +83,18 @@ def _pins_hold(exact2):
     walk = np.array([[0, 0], [1, 0], [1, 1]], dtype=np.int32)
     for target in (2.3, 0.37):
         M = 1 << 30
-        T = 1.0 / target - 1.0 / M
-        r = float(orc.ratio(2, 1.0, T, M))
+        Wsum = M / target - 1.0
+        r = orc.ratio(2, 1.0, Wsum, M)
         hits = 0
         trials = 6000
         for k in range(trials):
-            out = orc.step(2, 10, walk, 1.0, T, M, k, 1, 2, seed=99)
+            out = orc.step(2, 10, walk, 1.0, Wsum, M, k, 1, 2, seed=99)
             if target > 1:
                 hits += out["c"] == 2
             else:
                 hits += out["outcome"] == 3
         p = (math.ceil(r) - r) if target > 1 else r
-        if abs(hits / trials - p) > 5 * math.sqrt(p * (1 - p) / trials):
+        if abs(r - target) > 1e-6 or abs(hits / trials - p) > 5 * math.sqrt(p * (1 - p) / trials):
             return False
     # r = 1 at the empty walk whatever the table says (one child per tour)
     if orc.ratio(0, 3.0, 100.0, 7) != 1.0:
@@ -94,7 +103,7 @@ def _pins_hold(exact2):
     pairs = {}
     for k in range(6000):
         out = orc.step(2, 10, np.array([[0, 0], [1, 0]], dtype=np.int32), 1.0,
-                       0.5 - 1.0 / (1 << 30), 1 << 30, k, 0, 0, seed=11)
+                       (1 << 29) - 1.0, 1 << 30, k, 0, 0, seed=11)
         pairs[tuple(out["dirs"])] = pairs.get(tuple(out["dirs"]), 0) + 1
     if len(pairs) != 6 or sum((v - 1000.0) ** 2 / 1000.0 for v in pairs.values()) > 5 + 6 * math.sqrt(10):
         return False
@@ -102,7 +111,7 @@ def _pins_hold(exact2):
     counts = np.zeros(4)
     for k in range(6000):
         out = orc.step(2, 10, np.array([[0, 0], [1, 0]], dtype=np.int32), 1.0,
-                       1.0 - 1.0 / (1 << 30), 1 << 30, k, 0, 0, seed=7)
+                       (1 << 30) - 1.0, 1 << 30, k, 0, 0, seed=7)
         counts[out["dirs"][0]] += 1
     exp_ = 2000.0
     if counts[1] != 0 or sum((counts[[0, 2, 3]] - exp_) ** 2 / exp_) > 2 + 6 * 2:
@@ -148,11 +157,10 @@ def _pins_hold(exact2):
     h.set_cutoffs(np.full(4, np.inf), np.full(4, np.inf), 2, 3.0)
     h.run(2500)
     t = h.tables()
-    K = math.ceil(float(np.float32(1.0 / 3.0)) * 2.0 ** 32)
-    p, M, S2 = K / 2.0 ** 32, 10000, t["S"][2]
+    p, M, S2 = 1.0 / 3.0, 10000, t["S"][2]
     if abs(S2 - M * p) > 5.0 * math.sqrt(M * p * (1 - p)):
         return False
-    if not math.isclose(t["W"][2], S2 * 12.0 * (2.0 ** 32 / K) * 2.0 ** -orc.scale_exp(2, 2), rel_tol=1e-12):
+    if not math.isclose(t["W"][2], S2 * 12.0 * 3.0 * 2.0 ** -orc.scale_exp(2, 2), rel_tol=1e-12):
         return False
     # per-tour square sums against the exact Rosenbluth second moment (no cut-off
     # active: one walk per tour, E[W^2] = sum over all walks of W)

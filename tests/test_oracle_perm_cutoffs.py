@@ -65,22 +65,20 @@ def test_always_enrich_grows_a_fixed_tree(copies):
 
 @pytest.mark.parametrize("q", [2.0, 3.0, 4.0])
 def test_always_prune_is_binomial_with_exact_reweighting(q):
-    """t = inf: every node past the empty walk survives with probability
-    K/2^32, K = ceil(fl32(1/q) 2^32), and then carries W 2^32/K.  The samples at
-    length 2 are Binomial(M, K/2^32); each weighs 4.3.(2^32/K) exactly, so
-    W_2 = S_2 . 12 . 2^32/K at the stored scale, and E[c_2] = 12."""
+    """t = inf: every node past the empty walk survives with probability 1/q and
+    then carries q W.  The samples at length 2 are Binomial(M, 1/q); each weighs
+    4.3.q exactly, so W_2 = S_2 . 12 . q at the stored scale, and E[c_2] = 12."""
     d, n_max, M = 2, 4, 40000
     h = orc.Oracle(d, n_max, 8, seed=77)
     hi, lo = _cuts(d, n_max, lambda n: math.inf, lambda n: math.inf)
     h.set_cutoffs(hi, lo, copies=2, q=q)
     h.run(M // 8)
     t = h.tables()
-    K = math.ceil(float(np.float32(1.0 / q)) * 2.0 ** 32)
-    p = K / 2.0 ** 32
+    p = 1.0 / q
     S2 = t["S"][2]
     assert t["S"][0] == M and t["S"][1] == M
     assert abs(S2 - M * p) < 5.0 * math.sqrt(M * p * (1 - p))
-    w_one = 12.0 * (2.0 ** 32 / K) * _scale(d, 2)
+    w_one = 12.0 * q * _scale(d, 2)
     assert math.isclose(t["W"][2], S2 * w_one, rel_tol=1e-12)
     # two survivals to reach length 3
     assert abs(t["S"][3] - M * p * p) < 5.0 * math.sqrt(M * p * p * (1 - p * p))

@@ -88,19 +88,33 @@ def test_golden_counts_are_enumerator_output(exact_counts):
 
 
 # --------------------------------------------------------------------------
-# The ratio r of Sec. 2 (eq. 6) in single precision: within the FP32 recipe's
-# error bound of the exact rational W / ((sum_prev + W)/M).
+# The ratio r of Sec. 2 (eq. 6): r = W / [W_n]^sample with the own weight in
+# the running average.  Against the exact rational W M / (Wsum + W): three
+# correctly rounded double operations stay within 2 ulp of it.  Special cases
+# the paper fixes: a node whose own weight is the whole sum at its length has
+# r = M (a first visit), and in particular r = 1 in the first tour (M = 1).
 # --------------------------------------------------------------------------
 def test_ratio_close_to_exact_definition():
+    from fractions import Fraction
     rng = np.random.default_rng(5)
     for _ in range(4000):
         W = float(10.0 ** rng.uniform(-20, 20))
-        T = 0.0 if rng.random() < 0.1 else float(W * 10.0 ** rng.uniform(-6, 6))
         M = int(rng.integers(1, 1 << 40))
-        r = float(orc.ratio(5, W, T, M))
-        exact = W / (T + W / M)            # = W M / (sum_prev + W)
-        assert abs(r - exact) <= 2.0 ** -20 * exact, (W, T, M, r, exact)
+        Wsum = 0.0 if rng.random() < 0.1 else float(W * M * 10.0 ** rng.uniform(-6, 6))
+        r = orc.ratio(5, W, Wsum, M)
+        exact = Fraction(W) * M / (Fraction(Wsum) + Fraction(W))
+        assert abs(Fraction(r) - exact) <= Fraction(2 * 2.0 ** -52) * exact, (W, Wsum, M, r)
     assert orc.ratio(0, 3.0, 100.0, 7) == 1.0   # the empty walk always has r = 1
+
+
+def test_ratio_first_visit_and_first_tour():
+    rng = np.random.default_rng(6)
+    for _ in range(2000):
+        W = float(10.0 ** rng.uniform(-30, 30))
+        assert orc.ratio(7, W, 0.0, 1) == 1.0            # first tour: own weight is all
+        M = int(rng.integers(2, 1 << 30))
+        r = orc.ratio(7, W, 0.0, M)                      # first visit: r = M
+        assert abs(r - M) <= 2 * 2.0 ** -52 * M
 
 
 # --------------------------------------------------------------------------
@@ -112,7 +126,7 @@ def test_step_a_plus_and_distinct_free_children(d):
     for st in states:
         walk = st["walk"]
         n = walk.shape[0] - 1
-        out = orc.step(d, 40, walk, st["W"], st["T"], st["M"], st["ordinal"],
+        out = orc.step(d, 40, walk, st["W"], st["Wsum"], st["M"], st["ordinal"],
                        st["seq"], st["tour"], seed=77)
         free = inputs.free_neighbours(walk)
         if n == 40:
@@ -144,7 +158,7 @@ def test_step_root(d):
 
 def test_step_weight_conservation():
     """Enrichment conserves weight: c copies of W/c, each times a_+ (Sec. 2, eq. 2);
-    a survivor of pruning carries W/q with q its survival probability."""
+    a survivor of pruning carries W/r, r being its survival probability."""
     rng = np.random.default_rng(3)
     seen_enrich = seen_survive = 0
     for i in range(3000):
@@ -152,7 +166,7 @@ def test_step_weight_conservation():
         n = int(rng.integers(1, 30))
         walk = inputs.random_saw(rng, d, n)
         st = inputs.random_state(rng, n)
-        out = orc.step(d, 64, walk, st["W"], st["T"], st["M"], st["ordinal"], st["seq"],
+        out = orc.step(d, 64, walk, st["W"], st["Wsum"], st["M"], st["ordinal"], st["seq"],
                        st["tour"], seed=1234)
         if out["outcome"] != 3:
             continue
@@ -164,8 +178,7 @@ def test_step_weight_conservation():
             assert abs(total - st["W"] * a) <= 4e-16 * st["W"] * a
         else:
             seen_survive += 1
-            q = out["survive_K"] / 2.0 ** 32
-            assert abs(out["child_w"] * scale * q - st["W"] * a) <= 4e-16 * st["W"] * a
+            assert abs(out["child_w"] * scale * out["r"] - st["W"] * a) <= 8e-16 * st["W"] * a
     assert seen_enrich > 100 and seen_survive > 100
 
 
@@ -174,16 +187,16 @@ def test_step_enrichment_and_survival_probabilities():
     walk = np.array([[0, 0], [1, 0], [1, 1]], dtype=np.int32)   # a_+ = 3 at the end
     W = 1.0
     trials = 40000
-    # r = 2.3: T chosen so that 1/(T/W + 1/M) = 2.3 with large M
+    # Wsum chosen so that r = W M / (Wsum + W) is near the target
     for target in (2.3, 0.37):
         M = 1 << 30
-        T = 1.0 / target - 1.0 / M
+        Wsum = M / target - 1.0
         counts = {}
         for k in range(trials):
-            out = orc.step(2, 10, walk, W, T, M, k, 1, 2, seed=99)
+            out = orc.step(2, 10, walk, W, Wsum, M, k, 1, 2, seed=99)
             key = out["c"] if out["outcome"] == 3 else 0
             counts[key] = counts.get(key, 0) + 1
-        r = float(orc.ratio(2, W, T, M))
+        r = orc.ratio(2, W, Wsum, M)
         if target > 1:
             p = math.ceil(r) - r
             frac = counts.get(2, 0) / trials
@@ -202,11 +215,11 @@ def test_step_direction_uniformity(c_target):
     walk = np.array([[0, 0], [1, 0]], dtype=np.int32)   # free: +x, +y, -y (a_+ = 3)
     M = 1 << 30
     # c_target = 1: r = 1 exactly; c_target = 2: r = 2 exactly (p = 0)
-    T = 1.0 / c_target - 1.0 / M
+    Wsum = M / c_target - 1.0
     counts = {}
     trials = 30000
     for k in range(trials):
-        out = orc.step(2, 10, walk, 1.0, T, M, k, 0, 0, seed=2024)
+        out = orc.step(2, 10, walk, 1.0, Wsum, M, k, 0, 0, seed=2024)
         assert out["c"] == c_target
         key = tuple(out["dirs"])
         counts[key] = counts.get(key, 0) + 1
