@@ -11,7 +11,10 @@
  *   - Sec. 2, eq. (6) and the paragraphs after it: flatPERM ratio
  *     r = W / [W_n]^sample (own weight included), enrichment into c copies of
  *     weight W/c (c = floor r with probability ceil r - r, else ceil r),
- *     pruning with probability 1 - r and survival with weight W/r;
+ *     pruning with probability 1 - r and survival with weight W/r.  Every
+ *     decision equals the one taken on r evaluated in double precision as
+ *     defined (a single-precision estimate settles most nodes; the others
+ *     evaluate r exactly);
  *   - Sec. 3, Algorithm 2 and Fig. 1: N sequences grow concurrently and share
  *     one table W; Algorithm 1: N sequences with private tables.
  *
@@ -51,7 +54,7 @@ typedef struct perm_run_s *perm_handle;
 #define PERM_ALG1 1   /* N independent sequences, one table each */
 
 /* Where a node reads its threshold [W_n]^sample from (Algorithm 2). */
-#define PERM_THRESH_SNAPSHOT 0  /* per-SM copy of W_n/M, refreshed every refresh_ns (default) */
+#define PERM_THRESH_SNAPSHOT 0  /* per-SM copy of W_n and M, refreshed every refresh_ns (default) */
 #define PERM_THRESH_FRESH 1     /* global table read by the node's own atomic add (exact
                                    sequential flatPERM when N = 1) */
 
@@ -111,10 +114,9 @@ int perm_set_stream(perm_handle h, void *stream);
  *   - a node of length n >= 1 whose weight W exceeds T_hi[n] is enriched into
  *     `copies` copies, with distinct steps, at most a_+ of them, each carrying
  *     W/c for the c made;
- *   - one with W < t_lo[n] survives with probability 1/q (1/q rounded to single
- *     precision and taken as the integer threshold K = ceil((1/q) 2^32) on the
- *     node's first random word) and then carries W 2^32/K (= q W when 1/q is
- *     exact in single precision);
+ *   - one with W < t_lo[n] survives with probability 1/q (u0 < 1/q in double
+ *     precision, u0 being the node's first random word over 2^32) and then
+ *     carries q W;
  *   - otherwise it grows one copy, as in flatPERM with r = 1.
  * The empty walk is neither enriched nor pruned.  The shared table no longer
  * decides anything, so a run with sharing off (fresh thresholds, or
@@ -163,6 +165,27 @@ int perm_reset(perm_handle h);
  * Any pointer may be NULL.  Arrays have n_max+1 entries. */
 int perm_estimates(perm_handle h, double *log_cn, double *S_n, double *relvar_n);
 
+/* Estimates from raw tables, without a handle (host arithmetic only; no device
+ * call): e.g. tables pooled over several runs or replicas, or the per-sequence
+ * rows of an Algorithm-1 run.  W_n, Q_n: `rows` rows of n_max+1 doubles at the
+ * stored scale (as perm_tables returns them; Q_n may be NULL, then relvar_n is
+ * +inf); M: `rows` tour counts (each >= 1).  Per row, c = W_n/M is the sample
+ * average of Sec. 1, eq. 4, and (Q_n/M - c^2)/(M-1) its variance.
+ *   PERM_COMBINE_MEAN:      log_cn = log of the mean over rows of c (Sec. 3's
+ *                           average of the sequences' estimates; one row: eq. 4);
+ *                           relvar_n = the variance of that mean over its square;
+ *   PERM_COMBINE_GEOMETRIC: log_cn = the mean over rows of log c (the geometric
+ *                           combination Sec. 4 uses for Algorithm 1); relvar_n =
+ *                           the mean of the rows' relative variances / rows.
+ * log_cn adds E(n) log 2 back (-inf where an estimate is 0); relvar_n is +inf
+ * where a row has fewer than two tours.  Either output may be NULL.
+ * PERM_EINVAL on a bad argument (d, n_max < 0, rows < 1, a NULL W_n or M, an
+ * M below 1, an unknown combine). */
+#define PERM_COMBINE_MEAN 0
+#define PERM_COMBINE_GEOMETRIC 1
+int perm_estimates_from_tables(int d, int n_max, int rows, const double *W_n, const double *Q_n,
+                               const int64_t *M, int combine, double *log_cn, double *relvar_n);
+
 /* Raw tables after waiting: W_n, S_n, Q_n at the stored scale (the weight of a
  * walk of length n is stored divided by 2^E(n), E(n) = floor(11n/8) for d=2,
  * floor(9n/4) for d=3), and M.  Alg. 1 returns n_seq rows of n_max+1 and one
@@ -182,6 +205,9 @@ typedef struct {
     int64_t device_bytes; /* device memory held by the handle */
     int64_t tours_finished; /* tours whose copies have all been grown, cumulative */
     int64_t shared;       /* waiting copies handed to other walks, cumulative */
+    int64_t exact_steps;  /* nodes whose decision evaluated r in double precision because
+                             the single-precision estimate lay too close to a decision
+                             boundary to settle it, cumulative */
 } perm_stats_t;
 int perm_stats(perm_handle h, perm_stats_t *out);
 
@@ -197,16 +223,20 @@ int perm_observable_r2(perm_handle h, double *mean_r2, double *R_n);
 /* Sampled node trace (test support): every node whose DFS ordinal is a
  * multiple of `every`, in tours whose index within their sequence is a
  * multiple of `tour_every`, is recorded, up to `capacity` records, during later perm_run calls.
- * every = 0 switches tracing off.  perm_trace_read copies the records out
- * (see the layout in perm_trace_record). */
+ * every = 0 switches tracing off.  perm_trace_read copies the records out.
+ * Record: length n, a_plus, free_mask, c (copies; 0 when pruned), outcome (as
+ * perm_debug_step), exact (1 if the decision evaluated r in double precision),
+ * the chosen directions (-1 beyond c), the node's sequence, tour and DFS
+ * ordinal, the M it used, its weight W, the sum Wsum of the weights at its
+ * length that it saw (both at the stored scale), r as the decision used it
+ * (the single-precision estimate widened, or the exact r) and the children's
+ * weight (stored scale of length n+1). */
 typedef struct {
-    int32_t n, a_plus, free_mask, c, outcome, pad;
+    int32_t n, a_plus, free_mask, c, outcome, exact;
     int32_t dirs[6];
-    float r;
     uint32_t seq, tour;
-    uint32_t pad2;
-    uint64_t ordinal, M, survive_K;
-    double W, T, child_w;
+    uint64_t ordinal, M;
+    double W, Wsum, r, child_w;
 } perm_trace_record;
 int perm_trace_enable(perm_handle h, int64_t every, int64_t tour_every, int capacity);
 /* count: records written (may exceed capacity; only capacity are kept).
@@ -221,18 +251,22 @@ const char *perm_strerror(int code);
  * All arrays are DEVICE pointers owned by the caller:
  *   coords[B*(n_max+1)*d] int32  walk b: site k at (b*(n_max+1)+k)*d, origin first
  *   len[B]      int32   n, the length of walk b (0..n_max)
- *   W[B], T[B]  double  node weight and running average before it (stored scale)
- *   M[B]        uint64  tours started
+ *   W[B]        double  the node's weight (stored scale of length n)
+ *   Wsum[B]     double  sum of the weights recorded at length n before the node
+ *   M[B]        uint64  tours started (>= 1)
  *   ordinal[B]  uint64  DFS ordinal of the node; seq[B], tour[B] uint32
- *   out_i[B*10] int32   outcome, a_plus, free_mask, c, dirs[0..5]
- *   out_r[B]    float   r;  out_w[B] double child weight;  out_K[B] uint64
- * Outcomes: 0 walk at n_max, 1 trapped, 2 pruned, 3 children.
- * Requires d in {2,3} and n_max <= 512.  Queued on `stream`, not waited for. */
+ *   out_i[B*11] int32   outcome, a_plus, free_mask, c, dirs[0..5], exact
+ *   out_r[B]    double  r as the decision used it (estimate, or exact when exact = 1)
+ *   out_w[B]    double  the children's weight (stored scale of length n+1)
+ * force_exact = 1 takes every decision on r in double precision (0: the
+ * kernel's own path).  Outcomes: 0 walk at n_max, 1 trapped, 2 pruned,
+ * 3 children.  Requires d in {2,3} and n_max <= 512.  Queued on `stream`,
+ * not waited for. */
 int perm_debug_step(int d, int n_max, int B, const int32_t *coords, const int32_t *len,
-                    const double *W, const double *T, const uint64_t *M,
+                    const double *W, const double *Wsum, const uint64_t *M,
                     const uint64_t *ordinal, const uint32_t *seq, const uint32_t *tour,
-                    uint64_t seed, uint32_t run_id, int32_t *out_i, float *out_r,
-                    double *out_w, uint64_t *out_K, void *stream);
+                    uint64_t seed, uint32_t run_id, int force_exact, int32_t *out_i,
+                    double *out_r, double *out_w, void *stream);
 
 /* ---------------------------------------------------------------------------
  * Batched runs (many independent runs, one CUDA-graph launch).

@@ -35,8 +35,10 @@ EXPORTS = (
     "perm_trace_read", "perm_destroy", "perm_strerror", "perm_debug_step", "perm_debug_philox",
     "perm_run_static", "perm_set_cutoffs", "perm_save", "perm_load", "perm_get_config", "perm_batch_create", "perm_batch_create_persistent", "perm_batch_run", "perm_batch_size",
     "perm_batch_estimates", "perm_batch_stats", "perm_batch_destroy", "perm_autotune",
-    "perm_observable_r2",
+    "perm_observable_r2", "perm_estimates_from_tables",
 )
+PERM_COMBINE_MEAN = 0
+PERM_COMBINE_GEOMETRIC = 1
 
 
 class perm_config(C.Structure):
@@ -54,16 +56,15 @@ class perm_stats_t(C.Structure):
                 ("slots", C.c_int), ("ctas", C.c_int), ("lanes_per_warp", C.c_int),
                 ("warps_per_cta", C.c_int), ("hash_slots", C.c_int), ("status", C.c_int),
                 ("device_bytes", C.c_int64), ("tours_finished", C.c_int64),
-                ("shared", C.c_int64)]
+                ("shared", C.c_int64), ("exact_steps", C.c_int64)]
 
 
 class perm_trace_record(C.Structure):
     _fields_ = [("n", C.c_int32), ("a_plus", C.c_int32), ("free_mask", C.c_int32),
-                ("c", C.c_int32), ("outcome", C.c_int32), ("pad", C.c_int32),
-                ("dirs", C.c_int32 * 6), ("r", C.c_float), ("seq", C.c_uint32),
-                ("tour", C.c_uint32), ("pad2", C.c_uint32), ("ordinal", C.c_uint64),
-                ("M", C.c_uint64), ("survive_K", C.c_uint64), ("W", C.c_double),
-                ("T", C.c_double), ("child_w", C.c_double)]
+                ("c", C.c_int32), ("outcome", C.c_int32), ("exact", C.c_int32),
+                ("dirs", C.c_int32 * 6), ("seq", C.c_uint32), ("tour", C.c_uint32),
+                ("ordinal", C.c_uint64), ("M", C.c_uint64), ("W", C.c_double),
+                ("Wsum", C.c_double), ("r", C.c_double), ("child_w", C.c_double)]
 
 
 class PermError(RuntimeError):
@@ -96,6 +97,8 @@ def load(path: str = LIB_PATH):
     L.perm_run_sync.argtypes = [vp, i64]
     L.perm_reset.argtypes = [vp]
     L.perm_estimates.argtypes = [vp, dp, dp, dp]
+    L.perm_estimates_from_tables.argtypes = [C.c_int, C.c_int, C.c_int, dp, dp, C.POINTER(i64),
+                                             C.c_int, dp, dp]
     L.perm_observable_r2.argtypes = [vp, dp, dp]
     L.perm_tables.argtypes = [vp, dp, dp, dp, C.POINTER(i64)]
     L.perm_stats.argtypes = [vp, C.POINTER(perm_stats_t)]
@@ -106,7 +109,7 @@ def load(path: str = LIB_PATH):
     L.perm_destroy.restype = None
     L.perm_strerror.argtypes = [C.c_int]
     L.perm_strerror.restype = C.c_char_p
-    L.perm_debug_step.argtypes = [C.c_int, C.c_int, C.c_int] + [vp] * 8 + [u64, u32] + [vp] * 4 + [vp]
+    L.perm_debug_step.argtypes = [C.c_int, C.c_int, C.c_int] + [vp] * 8 + [u64, u32, C.c_int] + [vp] * 3 + [vp]
     L.perm_debug_philox.argtypes = [C.c_int, vp, C.POINTER(u32), vp]
     L.perm_run_static.argtypes = [C.POINTER(perm_config), i64, vp, vp, vp, C.POINTER(i64), vp]
     L.perm_batch_create.argtypes = [hp, C.POINTER(perm_config), C.POINTER(i64), C.c_int, C.c_int]
@@ -179,6 +182,27 @@ def perm_reset(h):
     _check(load().perm_reset(h), "perm_reset")
 
 
+def perm_estimates_from_tables(d, n_max, W, Q, M, combine=PERM_COMBINE_MEAN):
+    """(log c_n, relative variance) from raw tables at the stored scale: W, Q of
+    shape (rows, n_max+1) or (n_max+1,), Q may be None; M one count per row."""
+    W = np.ascontiguousarray(W, dtype=np.float64).reshape(-1)
+    rows = W.size // (n_max + 1)
+    if rows < 1 or rows * (n_max + 1) != W.size:
+        raise ValueError("W must hold whole rows of n_max+1")
+    Qa = None if Q is None else np.ascontiguousarray(Q, dtype=np.float64).reshape(-1)
+    if Qa is not None and Qa.size != W.size:
+        raise ValueError("Q must match W")
+    Ma = np.ascontiguousarray(M, dtype=np.int64).reshape(-1)
+    if Ma.size != rows:
+        raise ValueError("one tour count per row")
+    lc = np.zeros(n_max + 1)
+    rv = np.zeros(n_max + 1)
+    _check(load().perm_estimates_from_tables(d, n_max, rows, _dp(W), None if Qa is None else _dp(Qa),
+                                             Ma.ctypes.data_as(C.POINTER(C.c_int64)), combine,
+                                             _dp(lc), _dp(rv)), "perm_estimates_from_tables")
+    return lc, rv
+
+
 def perm_estimates(h, n_max: int):
     L = n_max + 1
     lc, S, rv = np.empty(L), np.empty(L), np.empty(L)
@@ -229,11 +253,11 @@ def perm_destroy(h):
         load().perm_destroy(h)
 
 
-def perm_debug_step(d, n_max, B, coords, length, W, T, M, ordinal, seq, tour, seed, run_id,
-                    out_i, out_r, out_w, out_K, stream=0):
+def perm_debug_step(d, n_max, B, coords, length, W, Wsum, M, ordinal, seq, tour, seed, run_id,
+                    force_exact, out_i, out_r, out_w, stream=0):
     """All array arguments are device pointers (ints), e.g. tensor.data_ptr()."""
-    _check(load().perm_debug_step(d, n_max, B, coords, length, W, T, M, ordinal, seq, tour,
-                                  seed, run_id, out_i, out_r, out_w, out_K, stream),
+    _check(load().perm_debug_step(d, n_max, B, coords, length, W, Wsum, M, ordinal, seq, tour,
+                                  seed, run_id, force_exact, out_i, out_r, out_w, stream),
            "perm_debug_step")
 
 

@@ -70,19 +70,14 @@ def alg1_combine(tables, d, mode="arithmetic"):
     uses for Algorithm 1's best estimate of log c_10000.  A length some sequence
     never reached gives -inf there.  By the inequality of arithmetic and geometric
     means the geometric form is never above the arithmetic one."""
-    import math
-    from .replicas import scale_exp
-    M = np.asarray(tables["M"], dtype=float).reshape(-1)
+    from . import _native
+    M = np.asarray(tables["M"], dtype=np.int64).reshape(-1)
     N = M.size
     W = np.asarray(tables["W"], dtype=float).reshape(N, -1)
     if np.any(M < 1):
         raise ValueError("every sequence needs a tour")
-    c = W / M[:, None]
-    L = W.shape[1]
-    shift = np.array([scale_exp(d, n) for n in range(L)], dtype=float) * math.log(2.0)
-    with np.errstate(divide="ignore"):
-        if mode == "arithmetic":
-            return np.log(c.mean(axis=0)) + shift
-        if mode == "geometric":
-            return np.log(c).mean(axis=0) + shift
-    raise ValueError("mode is 'arithmetic' or 'geometric'")
+    modes = {"arithmetic": _native.PERM_COMBINE_MEAN, "geometric": _native.PERM_COMBINE_GEOMETRIC}
+    if mode not in modes:
+        raise ValueError("mode is 'arithmetic' or 'geometric'")
+    lc, _ = _native.perm_estimates_from_tables(d, W.shape[1] - 1, W, None, M, modes[mode])
+    return lc

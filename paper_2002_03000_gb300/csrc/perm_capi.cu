@@ -33,7 +33,7 @@ struct perm_run_s {
     double *Wn = nullptr, *Qn = nullptr, *X = nullptr, *gstk_w = nullptr, *Rn = nullptr;
     unsigned long long *Sn = nullptr, *tickets = nullptr, *seq_M = nullptr;
     unsigned long long *steps = nullptr, *max_stack = nullptr, *copies = nullptr, *refreshes = nullptr, *trace_count = nullptr;
-    unsigned long long *iterations = nullptr, *finished = nullptr;
+    unsigned long long *iterations = nullptr, *finished = nullptr, *exact_steps = nullptr;
     uint32_t *gstk_meta = nullptr;
     int *status = nullptr;
     // shared copies
@@ -45,7 +45,8 @@ struct perm_run_s {
     unsigned int *dq_ready = nullptr, *dq_free = nullptr, *outst = nullptr, *tmaxn = nullptr;
     int *hungry = nullptr;
     double2 *cut = nullptr;        // original PERM's cut-offs (nullptr: flatPERM)
-    float r_hi = 1.0f, r_lo = 1.0f;
+    int cut_copies = 1;
+    double cut_q = 1.0;
     perm_trace_record *trace = nullptr;
     int32_t *trace_coords = nullptr;
     int trace_cap = 0;
@@ -78,7 +79,8 @@ int dalloc(perm_handle h, T **p, size_t count) {
 
 void free_all(perm_handle h) {
     void *ptrs[] = {h->Wn, h->Qn, h->Rn, h->X, h->gstk_w, h->Sn, h->tickets, h->seq_M, h->steps,
-                    h->max_stack, h->copies, h->refreshes, h->iterations, h->finished, h->trace_count, h->gstk_meta, h->status, h->trace,
+                    h->max_stack, h->copies, h->refreshes, h->iterations, h->finished, h->exact_steps,
+                    h->trace_count, h->gstk_meta, h->status, h->trace,
                     h->trace_coords, h->dq_cells, h->dq_head, h->dq_tail, h->dq_ready, h->dq_free, h->outst,
                     h->tmaxn, h->hungry, h->cut};
     for (void *p : ptrs) if (p) cudaFree(p);
@@ -295,6 +297,7 @@ int create_impl(perm_handle *out, const perm_config *cfg, const ForcedLayout *fo
     if (rc == PERM_OK) rc = dalloc(h, &h->refreshes, 1);
     if (rc == PERM_OK) rc = dalloc(h, &h->iterations, 1);
     if (rc == PERM_OK) rc = dalloc(h, &h->finished, 1);
+    if (rc == PERM_OK) rc = dalloc(h, &h->exact_steps, 1);
     if (rc == PERM_OK) rc = dalloc(h, &h->trace_count, 1);
     if (rc == PERM_OK) rc = dalloc(h, &h->status, 1);
     // shared copies: a ring of cells, each one waiting copy record plus the keys of the
@@ -365,6 +368,7 @@ static RunDev make_params(perm_handle h) {
     P.Wn = h->Wn; P.Sn = h->Sn; P.Qn = h->Qn; P.Rn = h->Rn; P.tickets = h->tickets; P.seq_M = h->seq_M;
     P.X = h->X; P.gstk_meta = h->gstk_meta; P.gstk_w = h->gstk_w;
     P.steps = h->steps; P.max_stack = h->max_stack; P.copies = h->copies; P.refreshes = h->refreshes; P.iterations = h->iterations;
+    P.exact_steps = h->exact_steps;
     P.finished = h->finished;
     P.ramp_c0 = h->cfg.ramp_c0 < 0 ? -1 : (long long)h->cfg.ramp_c0;
     P.ramp_gamma_q16 = (unsigned long long)(h->cfg.ramp_gamma * 65536.0);
@@ -375,7 +379,12 @@ static RunDev make_params(perm_handle h) {
     P.dq_head = h->dq_head; P.dq_tail = h->dq_tail; P.dq_ready = h->dq_ready; P.dq_free = h->dq_free;
     P.outst = h->outst; P.tmaxn = h->tmaxn; P.hungry = h->hungry;
     P.status = h->status;
-    P.cut = h->cut; P.r_hi = h->r_hi; P.r_lo = h->r_lo;
+    P.cut = h->cut;
+    P.cut_copies = h->cut_copies;
+    P.cut_q = h->cut_q;
+    P.cut_inv_q = 1.0 / h->cut_q;
+    // survive iff u0 < 1/q, i.e. w0 < 2^32 fl(1/q), i.e. w0 < ceil(2^32 fl(1/q)) (w0 integer)
+    P.cut_K = (unsigned long long)std::ceil(P.cut_inv_q * 4294967296.0);
     P.trace = (h->trace_every > 0) ? h->trace : nullptr;
     P.trace_coords = h->trace_coords; P.trace_count = h->trace_count; P.trace_cap = h->trace_cap;
     P.trace_every = h->trace_every > 0 ? h->trace_every : 1;
@@ -407,8 +416,8 @@ int perm_set_cutoffs(perm_handle h, const double *T_hi, const double *t_lo, int 
     cudaError_t e = cudaMemcpyAsync(h->cut, host.data(), sizeof(double2) * L, cudaMemcpyHostToDevice, h->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
     if (e != cudaSuccess) return to_code(e);
-    h->r_hi = (float)copies;
-    h->r_lo = (float)(1.0 / q);
+    h->cut_copies = copies;
+    h->cut_q = q;
     return PERM_OK;
 }
 
@@ -497,6 +506,7 @@ int perm_reset(perm_handle h) {
     if (e == cudaSuccess) e = cudaMemsetAsync(h->refreshes, 0, sizeof(unsigned long long), h->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(h->iterations, 0, sizeof(unsigned long long), h->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(h->finished, 0, sizeof(unsigned long long), h->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->exact_steps, 0, sizeof(unsigned long long), h->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(h->max_stack, 0, sizeof(unsigned long long), h->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(h->status, 0, sizeof(int), h->stream);
     if (e == cudaSuccess && h->last_status != PERM_OK)   // a stopped run may leave tour sums behind
@@ -518,6 +528,49 @@ int perm_reset(perm_handle h) {
     return PERM_OK;
 }
 
+int perm_estimates_from_tables(int d, int n_max, int rows, const double *W_n, const double *Q_n,
+                               const int64_t *M, int combine, double *log_cn, double *relvar_n) {
+    if ((d != 2 && d != 3) || n_max < 0 || rows < 1 || !W_n || !M) return PERM_EINVAL;
+    if (combine != PERM_COMBINE_MEAN && combine != PERM_COMBINE_GEOMETRIC) return PERM_EINVAL;
+    const size_t L = (size_t)n_max + 1;
+    const double log2 = std::log(2.0);
+    for (size_t n = 0; n < L; ++n) {
+        // per row: the sample average c = W_n / M (eq. 4, any M >= 1) and the
+        // per-tour variance of it, (Q_n / M - c^2) / (M - 1) (M >= 2)
+        double mean = 0.0, mlog = 0.0, var = 0.0, rvar = 0.0;
+        bool ok = Q_n != nullptr, any_zero = false;
+        for (int t = 0; t < rows; ++t) {
+            const int64_t m = M[t];
+            if (m < 1) return PERM_EINVAL;
+            const double c = W_n[(size_t)t * L + n] / (double)m;
+            mean += c;
+            if (c > 0.0) mlog += std::log(c); else any_zero = true;
+            if (m < 2 || !Q_n) { ok = false; continue; }
+            double v = (Q_n[(size_t)t * L + n] / (double)m - c * c) / (double)(m - 1);
+            if (v < 0.0) v = 0.0;
+            var += v;
+            if (c > 0.0) rvar += v / (c * c);
+        }
+        const double R = (double)rows;
+        const double shift = scale_exp_host(d, (int)n) * log2;
+        double lc, rv;
+        if (combine == PERM_COMBINE_MEAN) {
+            // the average of the rows' sample averages (Sec. 3; one row: eq. 4)
+            mean /= R;
+            lc = mean > 0.0 ? std::log(mean) + shift : -INFINITY;
+            rv = (ok && mean > 0.0) ? (var / (R * R)) / (mean * mean) : INFINITY;
+        } else {
+            // the mean of the rows' log sample averages (the geometric combination of
+            // Sec. 4); its variance to first order is the mean relative variance / rows
+            lc = any_zero ? -INFINITY : mlog / R + shift;
+            rv = (ok && !any_zero) ? rvar / (R * R) : INFINITY;
+        }
+        if (log_cn) log_cn[n] = lc;
+        if (relvar_n) relvar_n[n] = rv;
+    }
+    return PERM_OK;
+}
+
 int perm_estimates(perm_handle h, double *log_cn, double *S_n, double *relvar_n) {
     if (!h) return PERM_EINVAL;
     const size_t L = (size_t)h->cfg.n_max + 1, cnt = L * h->ntab;
@@ -525,26 +578,25 @@ int perm_estimates(perm_handle h, double *log_cn, double *S_n, double *relvar_n)
     std::vector<int64_t> M(h->ntab);
     int rc = perm_tables(h, W.data(), S.data(), Q.data(), M.data());
     if (rc != PERM_OK) return rc;
-    for (size_t n = 0; n < L; ++n) {
-        double est = 0.0, var = 0.0, s = 0.0;
-        bool ok = true;
-        for (int t = 0; t < h->ntab; ++t) {
-            const double w = W[t * L + n], q = Q[t * L + n];
-            s += S[t * L + n];
-            const int64_t m = M[t];
-            if (m < 1) { ok = false; continue; }
-            const double c = w / (double)m;       // the sample average (eq. 4), any M >= 1
-            est += c;
-            if (m < 2) { ok = false; continue; }  // the variance needs two tours
-            double v = (q / (double)m - c * c) / (double)(m - 1);
-            if (v < 0.0) v = 0.0;
-            var += v;
+    for (int t = 0; t < h->ntab; ++t) {
+        if (M[t] < 1) {                          // no tour yet: nothing estimated
+            for (size_t n = 0; n < L; ++n) {
+                if (log_cn) log_cn[n] = -INFINITY;
+                if (relvar_n) relvar_n[n] = INFINITY;
+                if (S_n) S_n[n] = 0.0;
+            }
+            return PERM_OK;
         }
-        est /= (double)h->ntab;
-        var /= (double)h->ntab * (double)h->ntab;
-        if (log_cn) log_cn[n] = est > 0.0 ? std::log(est) + scale_exp_host(h->cfg.d, (int)n) * std::log(2.0) : -INFINITY;
-        if (S_n) S_n[n] = s;
-        if (relvar_n) relvar_n[n] = (ok && est > 0.0) ? var / (est * est) : INFINITY;
+    }
+    rc = perm_estimates_from_tables(h->cfg.d, h->cfg.n_max, h->ntab, W.data(), Q.data(), M.data(),
+                                    PERM_COMBINE_MEAN, log_cn, relvar_n);
+    if (rc != PERM_OK) return rc;
+    if (S_n) {
+        for (size_t n = 0; n < L; ++n) {
+            double s = 0.0;
+            for (int t = 0; t < h->ntab; ++t) s += S[(size_t)t * L + n];
+            S_n[n] = s;
+        }
     }
     return PERM_OK;
 }
@@ -574,13 +626,14 @@ int perm_stats(perm_handle h, perm_stats_t *out) {
     if (!h || !out) return PERM_EINVAL;
     int st = sync_status(h);
     if (st < 0 && st != PERM_EOVERFLOW && st != PERM_ETIMEOUT) return st;
-    unsigned long long steps = 0, ms = 0, cp = 0, rf = 0, it = 0, fin = 0, shr = 0;
+    unsigned long long steps = 0, ms = 0, cp = 0, rf = 0, it = 0, fin = 0, shr = 0, ex = 0;
     if (copy_out(h, &steps, h->steps, 8) != cudaSuccess) return PERM_EDEVICE;
     if (copy_out(h, &cp, h->copies, 8) != cudaSuccess) return PERM_EDEVICE;
     if (copy_out(h, &rf, h->refreshes, 8) != cudaSuccess) return PERM_EDEVICE;
     if (copy_out(h, &it, h->iterations, 8) != cudaSuccess) return PERM_EDEVICE;
     if (copy_out(h, &ms, h->max_stack, 8) != cudaSuccess) return PERM_EDEVICE;
     if (copy_out(h, &fin, h->finished, 8) != cudaSuccess) return PERM_EDEVICE;
+    if (copy_out(h, &ex, h->exact_steps, 8) != cudaSuccess) return PERM_EDEVICE;
     if (h->share && copy_out(h, &shr, h->dq_tail, 8) != cudaSuccess) return PERM_EDEVICE;
     out->steps = (int64_t)steps;
     out->tours = h->cfg.alg == PERM_ALG2 ? h->tour_limit : h->seq_target * h->cfg.n_seq;
@@ -597,6 +650,7 @@ int perm_stats(perm_handle h, perm_stats_t *out) {
     out->device_bytes = h->device_bytes;
     out->tours_finished = (int64_t)fin;
     out->shared = (int64_t)shr;
+    out->exact_steps = (int64_t)ex;
     return PERM_OK;
 }
 
@@ -644,17 +698,18 @@ void perm_destroy(perm_handle h) {
 }
 
 int perm_debug_step(int d, int n_max, int B, const int32_t *coords, const int32_t *len,
-                    const double *W, const double *T, const uint64_t *M,
+                    const double *W, const double *Wsum, const uint64_t *M,
                     const uint64_t *ordinal, const uint32_t *seq, const uint32_t *tour,
-                    uint64_t seed, uint32_t run_id, int32_t *out_i, float *out_r,
-                    double *out_w, uint64_t *out_K, void *stream) {
+                    uint64_t seed, uint32_t run_id, int force_exact, int32_t *out_i,
+                    double *out_r, double *out_w, void *stream) {
     if ((d != 2 && d != 3) || n_max < 1 || n_max > 512 || B < 0) return PERM_EINVAL;
-    if (B > 0 && (!coords || !len || !W || !T || !M || !ordinal || !seq || !tour || !out_i ||
-                  !out_r || !out_w || !out_K))
+    if (force_exact != 0 && force_exact != 1) return PERM_EINVAL;
+    if (B > 0 && (!coords || !len || !W || !Wsum || !M || !ordinal || !seq || !tour || !out_i ||
+                  !out_r || !out_w))
         return PERM_EINVAL;
-    cudaError_t e = perm::launch_debug_step(d, n_max, B, coords, len, W, T, M, ordinal, seq, tour,
-                                            (uint32_t)seed ^ run_id, (uint32_t)(seed >> 32), out_i,
-                                            out_r, out_w, out_K, (cudaStream_t)stream);
+    cudaError_t e = perm::launch_debug_step(d, n_max, B, coords, len, W, Wsum, M, ordinal, seq, tour,
+                                            (uint32_t)seed ^ run_id, (uint32_t)(seed >> 32), force_exact,
+                                            out_i, out_r, out_w, (cudaStream_t)stream);
     return to_code(e);
 }
 
@@ -707,7 +762,7 @@ int member_reset(perm_handle h) {
 namespace {
 
 constexpr char kCkptMagic[8] = {'P', 'E', 'R', 'M', 'C', 'K', 'P', '1'};
-constexpr uint32_t kCkptVersion = 1;
+constexpr uint32_t kCkptVersion = 2;
 
 struct CkptHeader {
     char magic[8];
@@ -715,9 +770,9 @@ struct CkptHeader {
     uint32_t header_bytes;
     perm_config cfg;               // as the handle holds it (defaults filled in)
     int64_t tour_limit, seq_target;
-    int32_t ntab, has_rn, has_cut, pad0;
-    float r_hi, r_lo;
-    uint64_t steps, max_stack, copies, refreshes, iterations, finished;
+    int32_t ntab, has_rn, has_cut, cut_copies;
+    double cut_q;
+    uint64_t steps, max_stack, copies, refreshes, iterations, finished, exact_steps;
 };
 
 // Bytes of the arrays after the header, or 0 when the sizes make no sense.
@@ -749,8 +804,8 @@ int perm_save(perm_handle h, const char *path) {
     hd.ntab = h->ntab;
     hd.has_rn = h->Rn != nullptr;
     hd.has_cut = h->cut != nullptr;
-    hd.r_hi = h->r_hi;
-    hd.r_lo = h->r_lo;
+    hd.cut_copies = h->cut_copies;
+    hd.cut_q = h->cut_q;
     const size_t L = (size_t)h->cfg.n_max + 1, cnt = L * h->ntab;
     std::vector<double> W(cnt), Q(cnt), R(hd.has_rn ? cnt : 0);
     std::vector<unsigned long long> S(cnt), sM(h->cfg.n_seq);
@@ -761,9 +816,11 @@ int perm_save(perm_handle h, const char *path) {
     if (e == cudaSuccess && hd.has_rn) e = copy_out(h, R.data(), h->Rn, cnt * 8);
     if (e == cudaSuccess) e = copy_out(h, sM.data(), h->seq_M, sM.size() * 8);
     if (e == cudaSuccess && hd.has_cut) e = copy_out(h, cut.data(), h->cut, L * sizeof(double2));
-    unsigned long long *cnts[6] = {h->steps, h->max_stack, h->copies, h->refreshes, h->iterations, h->finished};
-    uint64_t *dst[6] = {&hd.steps, &hd.max_stack, &hd.copies, &hd.refreshes, &hd.iterations, &hd.finished};
-    for (int i = 0; e == cudaSuccess && i < 6; ++i) e = copy_out(h, dst[i], cnts[i], 8);
+    unsigned long long *cnts[7] = {h->steps, h->max_stack, h->copies, h->refreshes, h->iterations, h->finished,
+                                   h->exact_steps};
+    uint64_t *dst[7] = {&hd.steps, &hd.max_stack, &hd.copies, &hd.refreshes, &hd.iterations, &hd.finished,
+                        &hd.exact_steps};
+    for (int i = 0; e == cudaSuccess && i < 7; ++i) e = copy_out(h, dst[i], cnts[i], 8);
     if (e != cudaSuccess) return to_code(e);
     // write beside the target, then rename: a crash never leaves half a checkpoint
     const std::string tmp = std::string(path) + ".tmp";
@@ -825,15 +882,16 @@ int perm_load(perm_handle *out, const char *path) {
         rc = dalloc(h, &h->cut, L);
         if (rc != PERM_OK) { perm_destroy(h); return rc; }
         e = put(h->cut, L * sizeof(double2));
-        h->r_hi = hd.r_hi;
-        h->r_lo = hd.r_lo;
+        h->cut_copies = hd.cut_copies;
+        h->cut_q = hd.cut_q;
     }
     // the tour counter: Alg. 2 hands out tickets from the tours started so far
     const unsigned long long tickets = hd.cfg.alg == PERM_ALG2 ? (unsigned long long)hd.tour_limit : 0ull;
-    const uint64_t vals[7] = {hd.steps, hd.max_stack, hd.copies, hd.refreshes, hd.iterations, hd.finished, tickets};
-    unsigned long long *dev[7] = {h->steps, h->max_stack, h->copies, h->refreshes, h->iterations, h->finished,
-                                  h->tickets};
-    for (int i = 0; e == cudaSuccess && i < 7; ++i)
+    const uint64_t vals[8] = {hd.steps, hd.max_stack, hd.copies, hd.refreshes, hd.iterations, hd.finished,
+                              hd.exact_steps, tickets};
+    unsigned long long *dev[8] = {h->steps, h->max_stack, h->copies, h->refreshes, h->iterations, h->finished,
+                                  h->exact_steps, h->tickets};
+    for (int i = 0; e == cudaSuccess && i < 8; ++i)
         e = cudaMemcpyAsync(dev[i], &vals[i], 8, cudaMemcpyHostToDevice, h->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
     if (e != cudaSuccess) { perm_destroy(h); return to_code(e); }

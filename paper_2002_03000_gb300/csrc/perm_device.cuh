@@ -6,7 +6,7 @@
 //   Sec. 2, eq. (6) and the two paragraphs after it: r = W/[W_n]^sample with the
 //     own weight included; r >= 1 enriches into c copies (c = floor r with
 //     probability ceil r - r, else ceil r) of weight W/c; r < 1 prunes with
-//     probability 1 - r, a survivor carries W/r.
+//     probability 1 - r, a survivor's weight is multiplied by 1/r.
 //
 // Layout conventions shared by the kernels:
 //   - A walk's occupancy hash and its per-site slot list live in shared memory,
@@ -159,13 +159,27 @@ __device__ __forceinline__ int probe_neighbours(const Key *tab, int S, int lane,
 }
 
 // ---------------------------------------------------------------------------
-// The ratio r of Sec. 2 in single precision.  Doubles enter through their
-// mantissa rounded to 24 bits (nearest, ties to even; a carry bumps the
-// exponent) and their exponent.  The running average T (before the node's own
-// weight) is carried packed: low word = FP32 bits of the rounded mantissa in
-// [1, 2) (0 if T is zero or subnormal), high word = the biased exponent.
-// r = 1 / (T/W + 1/M): the own weight enters through 1/M, since
-// [W_n] = T + W/M.
+// The ratio r of Sec. 2 (eq. 6): r = W / [W_n]^sample, [W_n]^sample =
+// (Wsum + W) / M with Wsum the sum of the weights recorded at length n before
+// the node and M the tours started.
+//
+// The decision needs r only through comparisons (r >= 1, floor and ceil of r,
+// u0 < ceil(r) - r, u0 < r), so each node first takes them on a single-
+// precision estimate x of r and falls back to r evaluated exactly as defined,
+// in double precision, when x lies too close to a comparison's boundary to
+// settle it.  The decision then equals the one taken on the double-precision
+// r at every node.
+//
+// The estimate: x = M / (1 + Wsum/W), with the two doubles entering through
+// their mantissas rounded to 24 bits (nearest, ties to even; a carry bumps the
+// exponent) and their exponents, and every operation a correctly rounded
+// single-precision one.  Six roundings of relative size <= 2^-24 (the two
+// mantissas, the quotient, the sum 1 + rho, M and the final quotient) and the
+// three roundings of the double-precision r (<= 4 2^-53) give
+// |x - r| <= 6.01 2^-24 x; every margin below allows 7.02 2^-24 x.  Doubles
+// with no such bound (W zero, negative, subnormal or not finite; Wsum
+// negative, subnormal or not finite; Wsum/W above 2^100) set `odd` and take
+// the exact path.
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ uint32_t mant24_bits(unsigned long long b, int &ef) {
     const uint32_t hi = (uint32_t)(b >> 32) & 0xFFFFFu, lo = (uint32_t)b;
@@ -176,41 +190,33 @@ __device__ __forceinline__ uint32_t mant24_bits(unsigned long long b, int &ef) {
     return (127u << 23) | keep;
 }
 
-__device__ __forceinline__ unsigned long long pack_threshold(double T) {
-    const unsigned long long b = (unsigned long long)__double_as_longlong(T);
-    int ef = (int)((b >> 52) & 0x7FFull);
-    if (ef == 0) return 0ull;
-    const uint32_t fm = mant24_bits(b, ef);
-    return (unsigned long long)fm | ((unsigned long long)(uint32_t)ef << 32);
-}
-
-__device__ __forceinline__ double unpack_threshold(unsigned long long p) {
-    const uint32_t fm = (uint32_t)p;
-    if (fm == 0u) return 0.0;
-    const uint32_t ef = (uint32_t)(p >> 32);
-    const unsigned long long b = ((unsigned long long)ef << 52) |
-                                 ((unsigned long long)(fm & 0x7FFFFFu) << 29);
-    return __longlong_as_double((long long)b);
-}
-
-__device__ __forceinline__ float ratio_r(int n, double W, unsigned long long Tp,
-                                         unsigned long long M) {
-    // 1/M in FP32 (M rounded to nearest first; 32-bit conversion when it fits)
-    const float Mf = (M >> 32) ? __ull2float_rn(M) : __uint2float_rn((uint32_t)M);
-    const float inv_m = __frcp_rn(Mf);
-    const uint32_t tm = (uint32_t)Tp;
+__device__ __forceinline__ float ratio_estimate(double W, double Wsum, unsigned long long M, bool &odd) {
     const unsigned long long wb = (unsigned long long)__double_as_longlong(W);
-    const int ew0 = (int)((uint32_t)(wb >> 52) & 0x7FFu);
-    int ew = ew0;
-    const float fm_w = __uint_as_float(mant24_bits(wb, ew));
-    const float q = __fdiv_rn(__uint_as_float(tm | (tm == 0u ? (127u << 23) : 0u)), fm_w);
-    int e = (int)(uint32_t)(Tp >> 32) - ew;
-    e = e > 100 ? 100 : (e < -100 ? -100 : e);
-    float rho = __fmul_rn(q, __uint_as_float((uint32_t)(e + 127) << 23));
-    rho = (ew0 == 0) ? 1.2676506e30f : rho;          // W zero or subnormal: 2^100
-    rho = (tm == 0u) ? 0.0f : rho;                  // T zero: 0 (checked first)
-    const float r = __frcp_rn(__fadd_rn(rho, inv_m));
-    return n == 0 ? 1.0f : r;
+    const unsigned long long sb = (unsigned long long)__double_as_longlong(Wsum);
+    int ew = (int)((uint32_t)(wb >> 52) & 0x7FFu), es = (int)((uint32_t)(sb >> 52) & 0x7FFu);
+    const bool s_zero = (sb == 0ull);
+    bool bad = (wb >> 63) != 0ull || (sb >> 63) != 0ull || ew == 0 || ew == 0x7FF || es == 0x7FF ||
+               (es == 0 && !s_zero);
+    const float mw = __uint_as_float(mant24_bits(wb, ew));
+    const float ms = __uint_as_float(mant24_bits(sb, es));
+    const float q = __fdiv_rn(ms, mw);               // in (0.5, 2)
+    int e = es - ew;
+    bad = bad || (!s_zero && e > 100);
+    // below 2^-100 the ratio only moves 1 + rho by less than 2^-99
+    e = e < -100 ? -100 : (e > 100 ? 100 : e);
+    float rho = __fmul_rn(q, __uint_as_float((uint32_t)(e + 127) << 23));   // exact scaling
+    rho = s_zero ? 0.0f : rho;
+    const float s = __fadd_rn(1.0f, rho);
+    const float Mf = (M >> 32) ? __ull2float_rn(M) : __uint2float_rn((uint32_t)M);
+    odd = bad;
+    return __fdiv_rn(Mf, s);
+}
+
+// r exactly as defined, in double precision: three correctly rounded operations
+// in the definition's order.
+__device__ __forceinline__ double ratio_exact(double W, double Wsum, unsigned long long M) {
+    const double avg = __ddiv_rn(__dadd_rn(Wsum, W), __ull2double_rn(M));
+    return __ddiv_rn(W, avg);
 }
 
 // Stored-weight scale: weight of a length-n walk is kept divided by 2^E(n).
@@ -218,23 +224,7 @@ __device__ __forceinline__ int scale_exp(int d, int n) {
     return d == 2 ? (11 * n) >> 3 : (9 * n) >> 2;
 }
 
-// ---------------------------------------------------------------------------
-// Decision of one node (Sec. 2).  Inputs: a_+ (>= 1), free list packed 3 bits
-// per entry in direction order, r, Philox words w0 (decision) and w1 (steps).
-// Output: c (0 = pruned), the chosen directions packed 3 bits each (first =
-// the copy grown now), and the weight factor F with child weight = W * F at
-// the stored scale of length n+1.  aoc[dE_index][a*8+c] = (a/c) 2^-dE.
-// ---------------------------------------------------------------------------
-struct NodeDecision {
-    int c;
-    uint32_t dirs;
-    double F;        // enrichment: child weight factor (a/c) 2^-dE
-    double Fs;       // survival: 1/K = Fs (1 + e) with Fs = y0 the FP32 reciprocal of K ...
-    float e;         // ... and e = 1 - K y0 in FP32 (K has at most 24 significant bits)
-    bool survive;
-};
-
-// Exact float -> double widening by bit manipulation (normal floats).
+// Exact float -> double widening by bit manipulation (normal floats and zero).
 __device__ __forceinline__ double widen(float f) {
     const uint32_t b = __float_as_uint(f);
     if ((b & 0x7FFFFFFFu) == 0u) return 0.0;
@@ -244,65 +234,68 @@ __device__ __forceinline__ double widen(float f) {
     return __longlong_as_double((long long)d);
 }
 
-// w < ceil(x) for an integer w in [0, 2^32) and a float x in [0, 2^32], exactly,
-// with integer operations only (u0 < x/2^32  <=>  w < ceil(x)).
-__device__ __forceinline__ bool below_ceil(uint32_t w, float x) {
-    const uint32_t b = __float_as_uint(x);
-    const int e = (int)(b >> 23) - 127;
-    const uint32_t m = (b & 0x7FFFFFu) | 0x800000u;
-    const int sh = 23 - e;
-    const uint32_t c_small = (m + ((1u << (sh & 31)) - 1u)) >> (sh & 31);   // 0 <= e < 23
-    const uint32_t c_big = m << ((e - 23) & 31);                             // 23 <= e < 32
-    const uint32_t c = (e >= 23) ? c_big : c_small;
-    return (b == 0u) ? false : (e >= 32 ? true : (e < 0 ? (w == 0u) : (w < c)));
+// ---------------------------------------------------------------------------
+// The decision of Sec. 2 on the estimate x (enrichment: c = floor r iff
+// u0 < ceil(r) - r, at most a_+ copies; pruning: survive iff u0 < r, with
+// u0 = w0 2^-32).  Sets `amb` when x cannot settle it:
+//  - the branch: x >= 1 + 2^-19 gives r > 1, x <= 1 - 2^-19 gives r < 1;
+//  - x (1 - 2^-20) >= a_+ + 1 gives floor r > a_+, so c = a_+ whatever u0;
+//  - floor and ceil: x farther than x 2^-20 from an integer gives
+//    floor r = floor x;
+//  - the u0 comparisons, on w0 against the threshold P = (ceil x - x) 2^32 or
+//    P = x 2^32 (exact in single precision), which is within 1797 x of the
+//    threshold of r: |w0 - P| > 4096 x + 512 settles them (the 512 covers the
+//    rounding of w0 to single precision and of the difference, 128 each).
+// Returns c (0: pruned); `surv` marks a survivor of pruning.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ int decide_estimate(float x, int a, uint32_t w0, bool &surv, bool &amb) {
+    const float w0f = __uint2float_rn(w0);
+    const float margin = __fmaf_rn(x, 4096.0f, 512.0f);
+    int c = 0;
+    surv = false;
+    amb = false;
+    if (x >= 1.0f + 0x1p-19f) {
+        if (__fmul_rn(x, 1.0f - 0x1p-20f) >= (float)(a + 1)) {
+            c = a;
+        } else {
+            const float fl = floorf(x), ce = __fadd_rn(fl, 1.0f);
+            const float fr = __fsub_rn(x, fl), p = __fsub_rn(ce, x);          // both exact
+            const float dlt = __fsub_rn(w0f, __fmul_rn(p, 4294967296.0f));
+            amb = fminf(fr, p) <= __fmul_rn(x, 0x1p-20f) || fabsf(dlt) <= margin;
+            const float craw = dlt < 0.0f ? fl : ce;
+            c = (craw >= (float)a) ? a : (int)craw;
+        }
+    } else if (x <= 1.0f - 0x1p-19f) {
+        const float dlt = __fsub_rn(w0f, __fmul_rn(x, 4294967296.0f));
+        amb = fabsf(dlt) <= margin;
+        surv = dlt < 0.0f;
+        c = surv ? 1 : 0;
+    } else {
+        amb = true;
+    }
+    return c;
 }
 
-// ceil(x) for a float x in [0, 2^32] as a 64-bit integer (exact).
-__device__ __forceinline__ unsigned long long ceil_u64(float x) {
-    const uint32_t b = __float_as_uint(x);
-    if (b == 0u) return 0ull;
-    const int e = (int)(b >> 23) - 127;
-    const unsigned long long m = (b & 0x7FFFFFu) | 0x800000u;
-    if (e < 0) return 1ull;
-    if (e >= 23) return m << (e - 23);
-    const int sh = 23 - e;
-    return (m + ((1ull << sh) - 1ull)) >> sh;
+// The same decision on the double-precision r, with the comparisons taken on
+// doubles exactly as defined.
+__device__ __forceinline__ int decide_exact(double r, int a, uint32_t w0, bool &surv) {
+    const double u0 = __dmul_rn(__uint2double_rn(w0), 0x1p-32);             // exact
+    surv = false;
+    if (r >= 1.0) {
+        const double fl = floor(r), ce = ceil(r);
+        const double p = __dsub_rn(ce, r);
+        const double craw = (u0 < p) ? fl : ce;
+        return (craw >= (double)a) ? a : (int)craw;
+    }
+    surv = u0 < r;
+    return surv ? 1 : 0;
 }
 
-// K = ceil(r 2^32), the integer survival threshold of a pruning decision (r < 1);
-// 0 when r >= 1.  Only test records carry it.
-__device__ __forceinline__ unsigned long long survive_K(float r) {
-    return r >= 1.0f ? 0ull : ceil_u64(ceilf(__fmul_rn(r, 4294967296.0f)));
-}
-
-__device__ __forceinline__ NodeDecision decide(int a, uint32_t freelist, float r, uint32_t w0,
-                                               uint32_t w1, const double *aoc_row, int dE) {
-    NodeDecision o;
-    o.F = 0.0;
-    o.Fs = 0.0;
-    o.e = 0.0f;
-    o.survive = false;
-    (void)dE;
-    // enrichment: p = ceil(r) - r; c = floor(r) iff u0 < p; at most a_+ copies
-    const float fl = floorf(r), ce = ceilf(r);
-    const float xp = __fmul_rn(__fsub_rn(ce, r), 4294967296.0f);   // p 2^32, exact
-    const float craw = below_ceil(w0, xp) ? fl : ce;
-    const int c_en = (craw >= (float)a) ? a : (int)craw;
-    // pruning: survive iff u0 < r, i.e. w0 < K = ceil(r 2^32)
-    const float kf = ceilf(__fmul_rn(r, 4294967296.0f));           // K, at most 24 bits
-    const bool surv = below_ceil(w0, kf);
-    const bool enrich = r >= 1.0f;
-    o.c = enrich ? c_en : (surv ? 1 : 0);
-    o.survive = !enrich && surv;
-    o.F = aoc_row[a * 8 + (enrich ? c_en : 0)];
-    // 1/K = y0 (1 + e) to ~2^-46: y0 the FP32 reciprocal, e its FP32 residual
-    const float y0 = __frcp_rn(kf);
-    o.e = __fmaf_rn(-kf, y0, 1.0f);
-    o.Fs = widen(y0);
-    // partial Fisher-Yates: c distinct free steps, draws by multiply-high on w1
-    // (the draws form one dependent chain, so it stops after c of them)
+// Partial Fisher-Yates: c distinct free steps from the free list (3 bits per
+// entry), draws by multiply-high on w1 (one dependent chain, stopped after c).
+__device__ __forceinline__ uint32_t choose_steps(int c, int a, uint32_t freelist, uint32_t w1) {
     uint32_t x = w1, list = freelist;
-    for (int i = 0; i < o.c; ++i) {
+    for (int i = 0; i < c; ++i) {
         const uint32_t m = (uint32_t)(a - i);
         const unsigned long long prod = (unsigned long long)x * m;
         const int j = i + (int)(prod >> 32);
@@ -311,8 +304,7 @@ __device__ __forceinline__ NodeDecision decide(int a, uint32_t freelist, float r
         const uint32_t t = vi ^ vj;
         list ^= (t << (3 * i)) | (t << (3 * j));
     }
-    o.dirs = (o.c == 0) ? 0u : list;
-    return o;
+    return (c == 0) ? 0u : list;
 }
 
 }  // namespace perm

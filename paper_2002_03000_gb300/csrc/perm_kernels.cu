@@ -93,58 +93,56 @@ __host__ __device__ __forceinline__ size_t head_region_bytes(int n_max, bool sna
 }
 
 // Weight factors for the two scale steps dE of the lattice (row t: dE = dE_lo + t):
-// [a*8 + c] = (a/c) 2^-dE for c >= 1 (enrichment), [a*8 + 0] = a 2^(32-dE)
-// (survival, before the 1/K factor).
+// [a*8 + c] = (a/c) 2^-dE for c >= 1 (enrichment), [a*8 + 0] = a 2^-dE (exact).
 __device__ void fill_aoc(double *aoc, int d, int tid, int nthreads) {
     const int dE_lo = (d == 2) ? 1 : 2;
     for (int i = tid; i < 128; i += nthreads) {
         const int t = i >> 6, a = (i >> 3) & 7, c = i & 7;
         double v = 0.0;
-        if (a >= 1 && c >= 1) {
-            const double q = __ddiv_rn((double)a, (double)c);
-            const double s = __longlong_as_double((long long)((unsigned long long)(1023 - dE_lo - t) << 52));
-            v = __dmul_rn(q, s);
-        } else if (a >= 1) {
-            const double s = __longlong_as_double((long long)((unsigned long long)(1023 + 32 - dE_lo - t) << 52));
-            v = __dmul_rn((double)a, s);
-        }
+        const double s = __longlong_as_double((long long)((unsigned long long)(1023 - dE_lo - t) << 52));
+        if (a >= 1 && c >= 1) v = __dmul_rn(__ddiv_rn((double)a, (double)c), s);
+        else if (a >= 1) v = __dmul_rn((double)a, s);
         aoc[i] = v;
     }
 }
 
+// Original PERM's cut-offs (Sec. 2) as a node reads them: per length (T_n, t_n)
+// at the stored scale, the copies made above T_n, and below t_n the survival
+// threshold K (survive iff w0 < K, i.e. u0 < 1/q) and the factor q.
+struct Cutoffs {
+    const double2 *cut;        // nullptr: flatPERM
+    int copies;
+    double q, inv_q;
+    unsigned long long K;
+};
+
 struct NodeOut {
-    int outcome, a, mask;
-    float r;
-    NodeDecision dec;
+    int outcome, a, mask, c;
+    uint32_t dirs;
+    double r;            // r as the decision used it (single-precision estimate or exact)
     double child_w;
     bool overflow;
+    bool exact;          // the decision was taken on r in double precision
 };
 
 // One node's growth step (Sec. 1 and Sec. 2): a_+, r, decision, steps, child
-// weight.  Shared by the persistent kernel and the snapshot-state kernel.
+// weight.  Wsum: sum of the weights recorded at length n before this node;
+// M: tours started.  force_exact: take every decision on the double-precision r.
+// Shared by the persistent kernel and the snapshot-state kernel.
 template <int D, typename Key>
 __device__ __forceinline__ NodeOut grow_node(const Key *hash, int stride, int lane, int log2h, int n,
-                                             int n_max, int cx, int cy, int cz, double W,
-                                             unsigned long long Tp, unsigned long long M,
-                                             unsigned long long ordinal, uint32_t seq,
-                                             uint32_t tour, uint32_t k0, uint32_t k1,
+                                             int n_max, int cx, int cy, int cz, double W, double Wsum,
+                                             unsigned long long M, unsigned long long ordinal,
+                                             uint32_t seq, uint32_t tour, uint32_t k0, uint32_t k1,
                                              const double *aoc, int (&eslot)[2 * D],
-                                             const double2 *cut = nullptr, float r_hi = 1.0f,
-                                             float r_lo = 1.0f) {
+                                             const Cutoffs &cuts, bool force_exact = false) {
     NodeOut o;
-    o.a = 0; o.mask = 0; o.child_w = 0.0; o.overflow = false;
-    o.dec.c = 0; o.dec.dirs = 0u; o.dec.F = 0.0;
-    // three independent chains: the node's random block, r, and the probes
+    o.a = 0; o.mask = 0; o.c = 0; o.dirs = 0u; o.child_w = 0.0; o.overflow = false; o.exact = false;
+    // three independent chains: the node's random block, the estimate of r, and the probes
     const Philox4 w = philox4x32_10((uint32_t)ordinal, (uint32_t)(ordinal >> 32), tour, seq, k0, k1);
-    float r = ratio_r(n, W, Tp, M);
-    if (cut != nullptr && n > 0) {
-        // original PERM (Sec. 2, cut-offs T_n, t_n): the same decision rules with
-        // r = copies above T_n (c copies of W/c), r = 1/q below t_n (survive with
-        // probability 1/q, weight q W), r = 1 between them
-        const double2 tc = __ldg(cut + n);
-        r = W > tc.x ? r_hi : (W < tc.y ? r_lo : 1.0f);
-    }
-    o.r = r;
+    bool odd = false;
+    const float x = ratio_estimate(W, Wsum, M, odd);
+    o.r = n == 0 ? 1.0 : widen(x);
     if (n == n_max) { o.outcome = kLeafNmax; return o; }
     bool ovf = false;
     const int fm = probe_neighbours<D, Key>(hash, stride, lane, log2h, cx, cy, cz, eslot, ovf);
@@ -162,15 +160,51 @@ __device__ __forceinline__ NodeOut grow_node(const Key *hash, int stride, int la
     const int dE = scale_exp(D, n + 1) - scale_exp(D, n);
     const int dE_lo = (D == 2) ? 1 : 2;
     const double *row = aoc + 64 * (dE - dE_lo);
-    o.dec = decide(a, freelist, r, w.x, w.y, row, dE);
-    if (o.dec.c == 0) { o.outcome = kPruned; return o; }
-    if (o.dec.survive) {
-        // child = W a 2^(32-dE) / K = u (1 + e), u = W a 2^(32-dE) y0
-        const double u = __dmul_rn(__dmul_rn(W, row[a * 8]), o.dec.Fs);
-        o.child_w = __fma_rn(u, widen(o.dec.e), u);
+    const double a_sc = row[a * 8];                      // a_+ 2^-dE, exact
+    int c;
+    bool surv = false;
+    if (n == 0) {
+        c = 1;                                           // r = 1 at the empty walk
+        o.child_w = __dmul_rn(W, a_sc);
+    } else if (cuts.cut != nullptr) {
+        // original PERM (Sec. 2, cut-offs T_n, t_n): copies above T_n, survival with
+        // probability 1/q (weight times q) below t_n, one copy between them
+        const double2 tc = __ldg(cuts.cut + n);
+        if (W > tc.x) {
+            c = cuts.copies < a ? cuts.copies : a;
+            o.r = (double)cuts.copies;
+            o.child_w = __dmul_rn(W, row[a * 8 + c]);
+        } else if (W < tc.y) {
+            surv = (unsigned long long)w.x < cuts.K;
+            c = surv ? 1 : 0;
+            o.r = cuts.inv_q;
+            o.child_w = __dmul_rn(__dmul_rn(W, cuts.q), a_sc);
+        } else {
+            c = 1;
+            o.r = 1.0;
+            o.child_w = __dmul_rn(W, a_sc);
+        }
     } else {
-        o.child_w = __dmul_rn(W, o.dec.F);
+        bool amb = false;
+        c = decide_estimate(x, a, w.x, surv, amb);
+        if (amb || odd || force_exact) {
+            // the estimate cannot settle a comparison: r exactly as defined
+            const double R = ratio_exact(W, Wsum, M);
+            c = decide_exact(R, a, w.x, surv);
+            o.r = R;
+            o.exact = true;
+            if (surv) o.child_w = __dmul_rn(__dmul_rn(W, __ddiv_rn(1.0, R)), a_sc);
+            else if (c > 0) o.child_w = __dmul_rn(__ddiv_rn(W, (double)c), a_sc);
+        } else if (surv) {
+            // a survivor carries W/r = [W_n]^sample = (Wsum + W)/M
+            o.child_w = __dmul_rn(__ddiv_rn(__dadd_rn(Wsum, W), __ull2double_rn(M)), a_sc);
+        } else if (c > 0) {
+            o.child_w = __dmul_rn(W, row[a * 8 + c]);    // (W/c) a_+ 2^-dE
+        }
     }
+    if (c == 0) { o.outcome = kPruned; o.child_w = 0.0; return o; }
+    o.c = c;
+    o.dirs = choose_steps(c, a, freelist, w.y);
     o.outcome = kChildren;
     return o;
 }
@@ -215,11 +249,11 @@ __device__ __forceinline__ void grow_run(const RunDev &P, unsigned char *smem, c
     CtaHead *head = reinterpret_cast<CtaHead *>(smem);
     double *aoc = reinterpret_cast<double *>(smem + 64);
     unsigned char *p = smem + 64 + 1024;
-    unsigned long long *Tpack = nullptr;
+    double *Wsnap = nullptr;
     double *Wd = nullptr;
     unsigned int *Sd = nullptr;
     if (snapshot) {
-        Tpack = reinterpret_cast<unsigned long long *>(p); p += 8 * (size_t)L;
+        Wsnap = reinterpret_cast<double *>(p); p += 8 * (size_t)L;
         Wd = reinterpret_cast<double *>(p); p += 8 * (size_t)L;
         Sd = reinterpret_cast<unsigned int *>(p); p += align16(4 * (size_t)L);
     }
@@ -236,9 +270,7 @@ __device__ __forceinline__ void grow_run(const RunDev &P, unsigned char *smem, c
     if (snapshot) {
         unsigned long long Ms = *(volatile unsigned long long *)P.tickets;
         if ((long long)Ms > limit) Ms = (unsigned long long)limit;
-        const double invM = __ddiv_rn(1.0, (double)(Ms > 0ull ? Ms : 1ull));
-        for (int k = threadIdx.x; k < L; k += blockDim.x)
-            Tpack[k] = pack_threshold(__dmul_rn(*(volatile double *)(P.Wn + k), invM));
+        for (int k = threadIdx.x; k < L; k += blockDim.x) Wsnap[k] = *(volatile double *)(P.Wn + k);
         if (threadIdx.x == 0) head->Ms = Ms;
     }
     __syncthreads();
@@ -270,11 +302,8 @@ __device__ __forceinline__ void grow_run(const RunDev &P, unsigned char *smem, c
             }
             unsigned long long Ms = *(volatile unsigned long long *)P.tickets;
             if ((long long)Ms > limit) Ms = (unsigned long long)limit;
-            const double invM = __ddiv_rn(1.0, (double)(Ms > 0ull ? Ms : 1ull));
-            for (int k = lane; k < L; k += 32) {
-                const double Wg = *(volatile double *)(P.Wn + k);
-                *(volatile unsigned long long *)&Tpack[k] = pack_threshold(__dmul_rn(Wg, invM));
-            }
+            for (int k = lane; k < L; k += 32)
+                *(volatile double *)&Wsnap[k] = *(volatile double *)(P.Wn + k);
             if (lane == 0) *(volatile unsigned long long *)&head->Ms = Ms;
             if (P.share && lane == 0) {
                 // idle walks not yet served by a queued copy, split over the CTAs
@@ -336,6 +365,7 @@ __device__ __forceinline__ void grow_run(const RunDev &P, unsigned char *smem, c
     uint32_t *gmeta = P.gstk_meta + (size_t)sidx * P.n_max;
     double *gwt = P.gstk_w + (size_t)sidx * P.n_max;
     const unsigned lt_mask = (1u << lane) - 1u;
+    const Cutoffs cuts{P.cut, P.cut_copies, P.cut_q, P.cut_inv_q, P.cut_K};
     const int dE_lo = (D == 2) ? 1 : 2;
     (void)dE_lo;
 
@@ -348,7 +378,7 @@ __device__ __forceinline__ void grow_run(const RunDev &P, unsigned char *smem, c
     int un_lo = 0, un_hi = -1, pend_dir = 0, pend_depth = 0;
     bool tour_end = false;
     double pend_w = 0.0;
-    unsigned long long my_steps = 0ull, my_copies = 0ull;
+    unsigned long long my_steps = 0ull, my_copies = 0ull, my_exact = 0ull;
     int my_max_stack = 0;
     int cur_seq = -1;
     long long seq_t = 0;
@@ -597,15 +627,19 @@ __device__ __forceinline__ void grow_run(const RunDev &P, unsigned char *smem, c
 
         // ---------------- one node ----------------
         if (state == kNode) {
-            unsigned long long Tp, Mb;
+            // the sum of the weights recorded at this length before the node (a
+            // snapshot, or the global table's value returned by the node's own add)
+            // and the tours started, this one included
+            double Wsum;
+            unsigned long long Mb;
             if (snapshot) {
                 atomicAdd(&Wd[n], W);
                 atomicAdd(&Sd[n], 1u);
-                Tp = *(volatile unsigned long long *)&Tpack[n];
+                Wsum = *(volatile double *)&Wsnap[n];
                 const unsigned long long Ms = *(volatile unsigned long long *)&head->Ms;
                 Mb = Ms > g + 1ull ? Ms : g + 1ull;
             } else {
-                const double old = atomicAdd(&Wrow[n], W);
+                Wsum = atomicAdd(&Wrow[n], W);
                 atomicAdd(&Srow[n], 1ull);
                 if (P.alg == PERM_ALG2) {
                     unsigned long long Mt = *(volatile unsigned long long *)P.tickets;
@@ -614,7 +648,6 @@ __device__ __forceinline__ void grow_run(const RunDev &P, unsigned char *smem, c
                 } else {
                     Mb = (unsigned long long)seq_t + 1ull;
                 }
-                Tp = pack_threshold(__ddiv_rn(old, (double)Mb));
             }
             atomicAdd(P.X + (size_t)own * L + n, W);
             if (P.Rn != nullptr) {
@@ -628,24 +661,23 @@ __device__ __forceinline__ void grow_run(const RunDev &P, unsigned char *smem, c
             int eslot[2 * D];
 #pragma unroll
             for (int j = 0; j < 2 * D; ++j) eslot[j] = 0;
-            const NodeOut o = grow_node<D, Key>(hash, ST, lane, P.log2h, n, P.n_max, cx, cy, cz, W, Tp,
-                                                Mb, ordinal, seq, tour, P.key0, P.key1, aoc, eslot,
-                                                P.cut, P.r_hi, P.r_lo);
+            const NodeOut o = grow_node<D, Key>(hash, ST, lane, P.log2h, n, P.n_max, cx, cy, cz, W, Wsum,
+                                                Mb, ordinal, seq, tour, P.key0, P.key1, aoc, eslot, cuts);
             if (o.overflow) set_status(P.status, PERM_EOVERFLOW);
+            my_exact += o.exact ? 1ull : 0ull;
 
             if (P.trace != nullptr && (ordinal % (unsigned long long)P.trace_every) == 0ull &&
                 ((unsigned long long)tour % (unsigned long long)P.trace_tour_every) == 0ull) {
                 const unsigned long long idx = atomicAdd(P.trace_count, 1ull);
                 if (idx < (unsigned long long)P.trace_cap) {
                     perm_trace_record *rec = P.trace + idx;
-                    rec->n = n; rec->a_plus = o.a; rec->free_mask = o.mask; rec->c = o.dec.c;
-                    rec->outcome = o.outcome; rec->pad = 0;
+                    rec->n = n; rec->a_plus = o.a; rec->free_mask = o.mask; rec->c = o.c;
+                    rec->outcome = o.outcome; rec->exact = o.exact ? 1 : 0;
                     for (int i = 0; i < 6; ++i)
-                        rec->dirs[i] = (i < o.dec.c) ? (int)((o.dec.dirs >> (3 * i)) & 7u) : -1;
-                    rec->r = o.r; rec->seq = seq; rec->tour = tour; rec->pad2 = 0u;
+                        rec->dirs[i] = (i < o.c) ? (int)((o.dirs >> (3 * i)) & 7u) : -1;
+                    rec->seq = seq; rec->tour = tour;
                     rec->ordinal = ordinal; rec->M = Mb;
-                    rec->survive_K = (o.outcome == kPruned || o.outcome == kChildren) ? survive_K(o.r) : 0ull;
-                    rec->W = W; rec->T = unpack_threshold(Tp); rec->child_w = o.child_w;
+                    rec->W = W; rec->Wsum = Wsum; rec->r = o.r; rec->child_w = o.child_w;
                     int32_t *cc = P.trace_coords + (size_t)idx * L * D;
                     for (int k = 0; k < n; ++k) {
                         int x, y, z;
@@ -661,7 +693,7 @@ __device__ __forceinline__ void grow_run(const RunDev &P, unsigned char *smem, c
             if ((uint32_t)ordinal == 0xFFFFFFFFu) set_status(P.status, PERM_EOVERFLOW);
             ordinal += 1ull;
             if (o.outcome == kChildren) {
-                const int c = o.dec.c;
+                const int c = o.c;
                 my_copies += (unsigned long long)(c - 1);
                 if (c > 1) {
                     // copies 1..c-1 wait in one record (depth, count, steps, weight)
@@ -678,7 +710,7 @@ __device__ __forceinline__ void grow_run(const RunDev &P, unsigned char *smem, c
                     if (top >= P.n_max) {
                         set_status(P.status, PERM_EOVERFLOW);
                     } else {
-                        const uint32_t rest = (o.dec.dirs >> 3) & ((1u << (3 * (c - 1))) - 1u);
+                        const uint32_t rest = (o.dirs >> 3) & ((1u << (3 * (c - 1))) - 1u);
                         const int ti = top & (K - 1);
                         smeta[(uint32_t)ti * ST + lane] = (uint32_t)n | ((uint32_t)(c - 1) << 16) | (rest << 19);
                         sw[(uint32_t)ti * ST + lane] = o.child_w;
@@ -686,7 +718,7 @@ __device__ __forceinline__ void grow_run(const RunDev &P, unsigned char *smem, c
                         my_max_stack = top - bot > my_max_stack ? top - bot : my_max_stack;
                     }
                 }
-                const int dir0 = (int)(o.dec.dirs & 7u);
+                const int dir0 = (int)(o.dirs & 7u);
                 const int s0 = select_slot<D>(eslot, dir0);
                 step_coords(dir0, cx, cy, cz);
                 n += 1;
@@ -885,18 +917,20 @@ __device__ __forceinline__ void grow_run(const RunDev &P, unsigned char *smem, c
     if (P.share && lane == 0 && my_hungry != 0) atomicAdd(P.hungry, -my_hungry);
 
     // statistics, then tell the refresher this warp is done
-    unsigned long long tot = my_steps, cps = my_copies;
+    unsigned long long tot = my_steps, cps = my_copies, exn = my_exact;
     int ms = my_max_stack;
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) {
         tot += __shfl_xor_sync(kFull, tot, off);
         cps += __shfl_xor_sync(kFull, cps, off);
+        exn += __shfl_xor_sync(kFull, exn, off);
         const int o = __shfl_xor_sync(kFull, ms, off);
         ms = o > ms ? o : ms;
     }
     if (lane == 0) {
         atomicAdd(P.steps, tot);
         atomicAdd(P.copies, cps);
+        if (exn) atomicAdd(P.exact_steps, exn);
         atomicAdd(P.iterations, my_iters);
         atomicMax(P.max_stack, (unsigned long long)ms);
         __threadfence_block();
@@ -1052,9 +1086,9 @@ __global__ void batch_init_kernel(const BatchDev B) {
 // ---------------------------------------------------------------------------
 template <int D, typename Key>
 __global__ void __launch_bounds__(32) debug_step_kernel(int n_max, int log2h, int B,
-        const int32_t *coords, const int32_t *len, const double *Wv, const double *Tv,
+        const int32_t *coords, const int32_t *len, const double *Wv, const double *Wsv,
         const uint64_t *Mv, const uint64_t *ordv, const uint32_t *seqv, const uint32_t *tourv,
-        uint32_t k0, uint32_t k1, int32_t *out_i, float *out_r, double *out_w, uint64_t *out_K) {
+        uint32_t k0, uint32_t k1, int force_exact, int32_t *out_i, double *out_r, double *out_w) {
     extern __shared__ __align__(16) unsigned char smem[];
     const int H = 1 << log2h;
     Key *hash = reinterpret_cast<Key *>(smem);
@@ -1065,7 +1099,7 @@ __global__ void __launch_bounds__(32) debug_step_kernel(int n_max, int log2h, in
     __syncwarp();
     const int b = blockIdx.x * 32 + lane;
     if (b >= B) return;
-    int32_t *oi = out_i + (size_t)b * 10;
+    int32_t *oi = out_i + (size_t)b * 11;
     const int n = len[b];
     if (n < 0 || n > n_max) { oi[0] = -1; return; }
     const int32_t *cb = coords + (size_t)b * (n_max + 1) * D;
@@ -1077,17 +1111,18 @@ __global__ void __launch_bounds__(32) debug_step_kernel(int n_max, int log2h, in
     }
     const int cx = cb[n * D], cy = cb[n * D + 1], cz = (D == 3) ? cb[n * D + 2] : 0;
     int eslot[2 * D];
+    const Cutoffs none{nullptr, 1, 1.0, 1.0, 0ull};
     const NodeOut o = grow_node<D, Key>(hash, kStride, lane, log2h, n, n_max, cx, cy, cz, Wv[b],
-                                        pack_threshold(Tv[b]), Mv[b], ordv[b], seqv[b], tourv[b],
-                                        k0, k1, aoc, eslot);
+                                        Wsv[b], Mv[b], ordv[b], seqv[b], tourv[b], k0, k1, aoc, eslot,
+                                        none, force_exact != 0);
     oi[0] = (ovf || o.overflow) ? -2 : o.outcome;
     oi[1] = o.a;
     oi[2] = o.mask;
-    oi[3] = o.dec.c;
-    for (int i = 0; i < 6; ++i) oi[4 + i] = (i < o.dec.c) ? (int)((o.dec.dirs >> (3 * i)) & 7u) : -1;
+    oi[3] = o.c;
+    for (int i = 0; i < 6; ++i) oi[4 + i] = (i < o.c) ? (int)((o.dirs >> (3 * i)) & 7u) : -1;
+    oi[10] = o.exact ? 1 : 0;
     out_r[b] = o.r;
     out_w[b] = o.child_w;
-    out_K[b] = (o.outcome == kPruned || o.outcome == kChildren) ? survive_K(o.r) : 0ull;
 }
 
 __global__ void philox_kernel(int B, const uint32_t *ctr, uint32_t k0, uint32_t k1, uint32_t *out) {
@@ -1202,10 +1237,10 @@ cudaError_t launch_finalize(unsigned long long *tickets, long long limit, cudaSt
 }
 
 cudaError_t launch_debug_step(int d, int n_max, int B, const int32_t *coords, const int32_t *len,
-                              const double *W, const double *T, const uint64_t *M,
+                              const double *W, const double *Wsum, const uint64_t *M,
                               const uint64_t *ordinal, const uint32_t *seq, const uint32_t *tour,
-                              uint32_t key0, uint32_t key1, int32_t *out_i, float *out_r,
-                              double *out_w, uint64_t *out_K, cudaStream_t stream) {
+                              uint32_t key0, uint32_t key1, int force_exact, int32_t *out_i,
+                              double *out_r, double *out_w, cudaStream_t stream) {
     int log2h = 4;
     while ((1 << log2h) < 2 * n_max) ++log2h;
     const int blocks = (B + 31) / 32;
@@ -1216,14 +1251,14 @@ cudaError_t launch_debug_step(int d, int n_max, int B, const int32_t *coords, co
         cudaError_t e = cudaFuncSetAttribute(debug_step_kernel<2, uint32_t>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
-        debug_step_kernel<2, uint32_t><<<blocks, 32, smem, stream>>>(n_max, log2h, B, coords, len, W, T,
-                M, ordinal, seq, tour, key0, key1, out_i, out_r, out_w, out_K);
+        debug_step_kernel<2, uint32_t><<<blocks, 32, smem, stream>>>(n_max, log2h, B, coords, len, W, Wsum,
+                M, ordinal, seq, tour, key0, key1, force_exact, out_i, out_r, out_w);
     } else {
         cudaError_t e = cudaFuncSetAttribute(debug_step_kernel<3, uint32_t>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
-        debug_step_kernel<3, uint32_t><<<blocks, 32, smem, stream>>>(n_max, log2h, B, coords, len, W, T,
-                M, ordinal, seq, tour, key0, key1, out_i, out_r, out_w, out_K);
+        debug_step_kernel<3, uint32_t><<<blocks, 32, smem, stream>>>(n_max, log2h, B, coords, len, W, Wsum,
+                M, ordinal, seq, tour, key0, key1, force_exact, out_i, out_r, out_w);
     }
     return cudaGetLastError();
 }

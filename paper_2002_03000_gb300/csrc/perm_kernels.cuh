@@ -31,9 +31,12 @@ struct RunDev {
     double *Qn;
     double *Rn;                    // optional (nullptr: off): sum of W |omega_n|^2 per length
     // original PERM (nullptr: flatPERM): per length (T_n, t_n) at the stored scale; a node
-    // above T_n decides with r = r_hi (copies), one below t_n with r = r_lo (1/q)
+    // above T_n makes cut_copies copies, one below t_n survives iff its first random
+    // word is below cut_K = ceil(fl(1/q) 2^32) (u0 < 1/q) and then carries q W
     const double2 *cut;
-    float r_hi, r_lo;
+    int cut_copies;
+    double cut_q, cut_inv_q;
+    unsigned long long cut_K;
     unsigned long long *tickets;   // Alg. 2: tours started (M); Alg. 1: next sequence
     unsigned long long *seq_M;     // Alg. 1: tours done per sequence
     // per-walk scratch
@@ -46,6 +49,7 @@ struct RunDev {
     unsigned long long *copies;
     unsigned long long *refreshes;
     unsigned long long *iterations;
+    unsigned long long *exact_steps;   // nodes whose decision took r in double precision
     unsigned long long *finished;  // Alg. 2: tours finished (admission of new tours)
     long long ramp_c0;             // admission: in flight <= c0 + gamma * finished
     unsigned long long ramp_gamma_q16;
@@ -112,10 +116,10 @@ cudaError_t launch_finalize(unsigned long long *tickets, long long limit, cudaSt
 cudaError_t set_smem_limits();
 
 cudaError_t launch_debug_step(int d, int n_max, int B, const int32_t *coords, const int32_t *len,
-                              const double *W, const double *T, const uint64_t *M,
+                              const double *W, const double *Wsum, const uint64_t *M,
                               const uint64_t *ordinal, const uint32_t *seq, const uint32_t *tour,
-                              uint32_t key0, uint32_t key1, int32_t *out_i, float *out_r,
-                              double *out_w, uint64_t *out_K, cudaStream_t stream);
+                              uint32_t key0, uint32_t key1, int force_exact, int32_t *out_i,
+                              double *out_r, double *out_w, cudaStream_t stream);
 cudaError_t launch_debug_philox(int B, const uint32_t *ctr, uint32_t k0, uint32_t k1, uint32_t *out,
                                 cudaStream_t stream);
 

@@ -146,7 +146,7 @@ extern "C" int perm_run_static(const perm_config *cfg, int64_t tours_per_seq, do
     P.tickets = cnt + 0; P.seq_M = nullptr;
     P.X = X; P.gstk_meta = gmeta; P.gstk_w = gw;
     P.steps = cnt + 1; P.max_stack = cnt + 2; P.copies = cnt + 3; P.refreshes = cnt + 4;
-    P.iterations = cnt + 5; P.finished = cnt + 6;
+    P.iterations = cnt + 5; P.finished = cnt + 6; P.exact_steps = cnt + 9;
     P.status = reinterpret_cast<int *>(cnt + 7);
     P.ramp_c0 = cfg->ramp_c0 < 0 ? -1 : (cfg->ramp_c0 == 0 ? 2 : cfg->ramp_c0);
     P.ramp_gamma_q16 = (unsigned long long)((cfg->ramp_gamma == 0.0 ? 0.25 : cfg->ramp_gamma) * 65536.0);

@@ -65,25 +65,18 @@ def pool_tables(tables: dict, device=None) -> dict:
     return dict(W=f[:L].copy(), S=f[L:2 * L].copy(), Q=f[2 * L:].copy(), M=m.cpu().numpy())
 
 
-def scale_exp(d: int, n: int) -> int:
-    """Exponent of the stored weight scale (stored = W / 2^E(n)), as the library
-    stores it: floor(11 n / 8) on the square lattice, floor(9 n / 4) on the cubic."""
-    return (11 * n) // 8 if d == 2 else (9 * n) // 4
-
-
 def estimates(tables: dict, d: int):
     """(log c_n, S_n, relative variance of c_n) from raw Algorithm-2 tables,
-    pooled or not: c_n = W_n / M (eq. 4), var = (Q_n / M - c_n^2) / (M - 1)."""
-    W, S, Q = (np.asarray(tables[k], dtype=np.float64) for k in ("W", "S", "Q"))
-    M = int(np.asarray(tables["M"]).reshape(-1)[0])
+    pooled or not, by the library's perm_estimates_from_tables (eq. 4 on the
+    pooled sums: c_n = W_n / M, var = (Q_n / M - c_n^2) / (M - 1))."""
+    from . import _native
+    W = np.asarray(tables["W"], dtype=np.float64)
+    S = np.asarray(tables["S"], dtype=np.float64)
+    M = np.asarray(tables["M"], dtype=np.int64).reshape(-1)
     L = W.size
-    lc = np.full(L, -math.inf)
-    rv = np.full(L, math.inf)
-    if M >= 1:
-        c = W / float(M)
-        pos = c > 0.0
-        lc[pos] = np.log(c[pos]) + np.array([scale_exp(d, n) for n in range(L)])[pos] * math.log(2.0)
-        if M >= 2:
-            var = np.maximum((Q / float(M) - c * c) / float(M - 1), 0.0)
-            rv[pos] = var[pos] / (c[pos] * c[pos])
+    if M.size != 1:
+        raise ValueError("estimates take Algorithm-2 tables (one row)")
+    if M[0] < 1:
+        return np.full(L, -math.inf), S.copy(), np.full(L, math.inf)
+    lc, rv = _native.perm_estimates_from_tables(d, L - 1, W, tables["Q"], M)
     return lc, S.copy(), rv

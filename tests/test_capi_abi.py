@@ -49,7 +49,7 @@ def test_argument_checks_need_no_device(lib):
     assert L.perm_create(ctypes.byref(h), 2, 0, 1, 1) == _native.PERM_EINVAL
     assert L.perm_create(ctypes.byref(h), 2, 10, 0, 1) == _native.PERM_EINVAL
     assert L.perm_run(None, 5) == _native.PERM_EINVAL
-    assert L.perm_debug_step(2, 600, 1, *([None] * 8), 0, 0, *([None] * 4), None) == _native.PERM_EINVAL
+    assert L.perm_debug_step(2, 600, 1, *([None] * 8), 0, 0, 0, *([None] * 3), None) == _native.PERM_EINVAL
     L.perm_destroy(None)   # NULL-safe
 
 
