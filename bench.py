@@ -70,23 +70,34 @@ def kernel_sources_sha256(texts=None):
     return h.hexdigest()
 
 
-def measured_traffic():
-    """DRAM bytes (read + write) of one growth-kernel launch of this workload, from
-    the ncu capture summarised in profiles/, if it was taken on the current kernel
-    sources; None otherwise (a stale count would mislead)."""
+def measured_counters():
+    """From the ncu capture summarised in profiles/ (if taken on the current kernel
+    sources): DRAM bytes (read + write) of one growth-kernel launch of this workload
+    and warp instructions per growth step; (None, None, why) otherwise (a stale count
+    would mislead)."""
     import re
     path = os.path.join(ROOT, "profiles", "grow_kernel_c2_traffic.md")
     try:
         text = open(path).read()
     except OSError:
-        return None, "no capture"
+        return None, None, "no capture"
     b = re.search(r"^bytes_per_launch:\s*(\d+)\s*$", text, re.M)
+    i = re.search(r"^warp_inst_per_step:\s*([0-9.]+)\s*$", text, re.M)
     h = re.search(r"^kernel_sources_sha256:\s*([0-9a-f]{64})\s*$", text, re.M)
     if not b or not h:
-        return None, "capture summary unreadable"
+        return None, None, "capture summary unreadable"
     if h.group(1) != kernel_sources_sha256():
-        return None, "kernel changed since the capture"
-    return int(b.group(1)), "ncu capture of the current kernel (profiles/grow_kernel_c2_traffic.md)"
+        return None, None, "kernel changed since the capture"
+    return (int(b.group(1)), float(i.group(1)) if i else None,
+            "ncu capture of the current kernel (profiles/grow_kernel_c2_traffic.md)")
+
+
+def sm_count():
+    try:
+        import torch
+        return torch.cuda.get_device_properties(0).multi_processor_count
+    except Exception:
+        return 152
 
 
 def measured_peaks():
@@ -165,25 +176,49 @@ def dist_env():
     return world, rank, local
 
 
+def host_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except Exception:
+        return os.cpu_count() or 1
+
+
 def cpu_baseline(seconds=15.0):
-    """The oracle, as it stands, on the host: the first tours of the benchmark
-    workload's sequences (single thread), until `seconds` of CPU work."""
+    """The oracle, as it stands, on the host cores: Algorithm 2 on every host core
+    (the paper's own form, Sec. 3: threads growing sequences that share the table,
+    updated atomically), the benchmark workload from empty tables in rounds of 8
+    tours per sequence until `seconds` of work; and the sequential oracle (one
+    thread) for a third of that."""
     from oracle import oracle as orc
     w = WORKLOAD
+    cores = host_cores()
     o = orc.Oracle(w["d"], w["n_max"], w["n_seq"], w["seed"])
     t0 = time.perf_counter()
     rounds = 0
     while True:
-        o.run(1)           # one more tour of each of the 4096 sequences
+        o.run_threads(8, cores)          # 8 more tours of each of the 4096 sequences
         rounds += 1
         el = time.perf_counter() - t0
         if el >= seconds:
             break
     steps = o.tables()["steps"]
-    return {"value": steps / el, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": "first %d tour(s) of each of the 4096 sequences of the workload "
-                      "(%d tours, %d growth steps) in %.1f s, one host thread"
-                      % (rounds, rounds * w["n_seq"], steps, el)}
+    o1 = orc.Oracle(w["d"], w["n_max"], w["n_seq"], w["seed"])
+    t1 = time.perf_counter()
+    r1 = 0
+    while True:
+        o1.run(1)
+        r1 += 1
+        el1 = time.perf_counter() - t1
+        if el1 >= seconds / 3.0:
+            break
+    steps1 = o1.tables()["steps"]
+    return {"value": steps / el, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": "Algorithm 2 on %d host threads sharing the table: the first %d tours of each of "
+                      "the 4096 sequences of the workload from empty tables (%d growth steps) in %.1f s"
+                      % (cores, 8 * rounds, steps, el),
+            "single_thread": {"value": steps1 / el1, "unit": UNIT, "cores": 1,
+                              "sample": "sequential oracle: the first %d tour(s) of each sequence "
+                                        "(%d growth steps) in %.1f s" % (r1, steps1, el1)}}
 
 
 def batched_vs_plain(tours):
@@ -399,35 +434,110 @@ def served_vs_one_at_a_time():
     return out
 
 
+REFERENCE_TOURS = 64
+
+
 def run_reference(args):
+    """The oracle on the host cores: each step is a bounded sample of the workload,
+    the first REFERENCE_TOURS tours of each of its 4096 sequences from empty tables,
+    grown by Algorithm 2 on every host core (threads sharing the table, as the
+    paper ran it).  Steps per tour are reported beside the GPU arm's."""
     world, rank, _ = dist_env()
     if rank != 0:
         return 0
     from oracle import oracle as orc
     w = WORKLOAD
-    tours_per_step = 1   # a bounded sample: one tour of each of the 4096 sequences
-    tot_steps, tot_t = 0, 0.0
+    cores = host_cores()
+    tot_steps, tot_t, tot_tours = 0, 0.0, 0
     for it in range(args.warmup + args.steps):
-        o = orc.Oracle(w["d"], w["n_max"], w["n_seq"], w["seed"])
+        o = orc.Oracle(w["d"], w["n_max"], w["n_seq"], w["seed"], run=it)
         t0 = time.perf_counter()
-        o.run(tours_per_step)
+        o.run_threads(REFERENCE_TOURS, cores)
         el = time.perf_counter() - t0
         if it >= args.warmup:
             tot_steps += o.tables()["steps"]
             tot_t += el
+            tot_tours += REFERENCE_TOURS * w["n_seq"]
     val = tot_steps / tot_t
+    sample = ("each step: the first %d tours of each of the 4096 sequences from empty tables, "
+              "Algorithm 2 on %d host threads sharing the table" % (REFERENCE_TOURS, cores))
     line = {"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * tot_t / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic (the lattice is the input)",
-            "config": {"workload": WORKLOAD_NAME, "sample": "each step: the first tour of each of "
-                       "the 4096 sequences, from empty tables", "cache": "host CPU"},
-            "cpu_baseline": {"value": val, "unit": UNIT, "cores": 1, "kind": "oracle",
-                             "sample": "each step: 4096 tours (one per sequence) of the workload, "
-                                       "one host thread"},
+            "config": {"workload": WORKLOAD_NAME, "d": w["d"], "n_max": w["n_max"],
+                       "sequences": w["n_seq"], "tours_per_seq": REFERENCE_TOURS, "seed": w["seed"],
+                       "steps_per_tour": tot_steps / tot_tours, "cache": "host CPU",
+                       "sample": sample},
+            "cpu_baseline": {"value": val, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": sample},
             "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
+
+
+def time_to_target(run, cap_s):
+    """Time to a target error, measured on the GPU:
+    - the benchmark workload (square, n_max 512, 4096 sequences), one run from empty
+      tables continued in chunks of 256 tours per sequence until the relative
+      standard error of c_512 (per-tour variance) is at most 1e-3, or `cap_s`; the
+      1e-4 time of the metric is extrapolated from it (error ~ 1/sqrt(tours)) and
+      labelled so;
+    - the exact-count workload (square, n_max 16, 12 sequences), one run continued
+      in chunks of 2e4 tours per sequence until the true error
+      max_n |c_n(estimate)/c_n - 1| over n <= 16 (exact c_n) is at most 1e-4, or
+      `cap_s`.
+    Wall clock, each chunk waited for (the estimates are read after every chunk)."""
+    import numpy as np
+    import torch
+    import paper_2002_03000_gb300 as pg
+    from paper_2002_03000_gb300 import _native as nat
+    w = WORKLOAD
+    out = {}
+    run.reset()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    rel, chunks = float("inf"), 0
+    while time.perf_counter() - t0 < cap_s:
+        nat.perm_run(run.h, w["tours"])
+        chunks += 1
+        rv = nat.perm_estimates(run.h, w["n_max"])[2]
+        rel = math.sqrt(rv[w["n_max"]])
+        if rel <= 1e-3:
+            break
+    el = time.perf_counter() - t0
+    out["bench_workload_rel_se_1e-3"] = {
+        "workload": WORKLOAD_NAME + ", continued", "target": "rel. SE of c_512 <= 1e-3",
+        "reached": rel <= 1e-3, "seconds": el, "rel_se_at_end": rel,
+        "tours_per_seq": chunks * w["tours"], "cap_s": cap_s, "kind": "measured"}
+    out["bench_workload_rel_se_1e-4"] = {
+        "target": "rel. SE of c_512 <= 1e-4", "seconds": el * (rel / 1e-4) ** 2,
+        "kind": "extrapolated from the measured run above (standard error ~ 1/sqrt(tours))"}
+    exact = np.array(EXACT_C_SQUARE, dtype=float)
+    r1 = pg.Run(2, 16, 12, 1, max_seconds=600.0)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    err, chunks, trail = float("inf"), 0, []
+    while time.perf_counter() - t0 < cap_s:
+        r1.run(20000)
+        chunks += 1
+        lc = r1.estimates()[0]
+        err = float(np.max(np.abs(np.exp(lc[:17] - np.log(exact)) - 1.0)))
+        trail.append(err)
+        if err <= 1e-4:
+            break
+    el = time.perf_counter() - t0
+    st = r1.stats()
+    r1.close()
+    out["exact_count_workload_true_error_1e-4"] = {
+        "workload": "plain flatPERM, d=2, n_max=16, 12 interacting sequences, chunks of 2e4 tours "
+                    "per sequence, seed 1",
+        "target": "max over n <= 16 of |c_n(estimate)/c_n(exact) - 1| <= 1e-4",
+        "reached": err <= 1e-4, "seconds": el, "error_at_end": err, "cap_s": cap_s,
+        "tours_per_seq": chunks * 20000, "steps": st["steps"], "steps_per_s": st["steps"] / el,
+        "error_after_each_chunk": trail[:8] + (["..."] if len(trail) > 9 else []) + trail[-1:],
+        "kind": "measured" if err <= 1e-4 else "not reached within the cap"}
+    return out
 
 
 def run_ours(args):
@@ -520,46 +630,27 @@ def run_ours(args):
     pooled = replicas.estimates(replicas.pool_tables(run.tables(), device="cuda"), w["d"])
     d2h = 3 * L * 8 + 4 + 8 * 3 + 8   # W_n, S_n, Q_n tables, status, counters, M
 
-    # ---- time to 1e-4 relative standard error of c_{n_max}, continuing one run ----
-    # The run continues in chunks of 256 tours per sequence for up to
-    # --target-cap-s seconds.  If 1e-4 is not reached, the time is extrapolated
-    # from the last chunk with the 1/sqrt(tours) law of the standard error.
+    # ---- time to target error, measured ----
     ttt = None
     if rank == 0 and not args.skip_time_to_target:
-        run.reset()
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        rel = float("inf")
-        chunks = 0
-        while time.perf_counter() - t0 < args.target_cap_s:
-            nat.perm_run(run.h, w["tours"])
-            chunks += 1
-            lc_t, S_t, rv_t = nat.perm_estimates(run.h, w["n_max"])
-            rel = math.sqrt(rv_t[w["n_max"]])
-            if rel <= 1e-4:
-                break
-        el = time.perf_counter() - t0
-        reached = rel <= 1e-4
-        ttt = {"target_rel_se_c_nmax": 1e-4, "reached": reached,
-               "seconds": el if reached else el * (rel / 1e-4) ** 2,
-               "measured_seconds": el, "rel_se_at_end": rel, "tours_per_seq": chunks * w["tours"],
-               "kind": "measured" if reached else "extrapolated from the measured run (se ~ 1/sqrt(tours))",
-               "note": "one run continued in chunks of 256 tours/sequence; relative standard "
-                       "error of c_512 from the per-tour variance"}
+        ttt = time_to_target(run, args.target_cap_s)
 
     f = copies_total / max(steps_total, 1)
     B = bytes_per_step(w["d"], f)
     avg_kern_s = sum(kern_ms) / len(kern_ms) / 1000.0
     steps_per_launch = steps_total / args.steps
     peak, peak_kind = measured_peaks()
-    traffic, traffic_src = measured_traffic()
+    traffic, inst_per_step, traffic_src = measured_counters()
     achieved = B * steps_per_launch / avg_kern_s / 1e9
     clk = clocks.summary()
-    if rank != 0:
-        run.close()
-        if world > 1:
-            torch.distributed.destroy_process_group()
-        return 0
+    issue = None
+    if inst_per_step is not None and clk.get("sm_mhz"):
+        # warp instructions issued per second against one per scheduler per cycle
+        ach = inst_per_step * steps_per_launch / avg_kern_s
+        pk = 4.0 * sm_count() * clk["sm_mhz"] * 1e6
+        issue = {"achieved": ach, "peak": pk, "unit": "warp instructions/s", "frac": ach / pk,
+                 "inst_per_step": inst_per_step, "source": traffic_src,
+                 "peak_basis": "4 schedulers x %d SMs x median sampled SM clock" % sm_count()}
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1000.0 * t_dev / args.steps,
@@ -573,9 +664,13 @@ def run_ours(args):
         "gpu_launches": 2 * args.steps,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": d2h},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak, "traffic": traffic, "traffic_source": traffic_src,
+                     "frac": achieved / peak,
+                     "traffic": traffic,
+                     "traffic_source": traffic_src,
                      "peak_source": peak_kind, "bytes_per_step": B, "copies_per_step": f,
-                     "kernel_ms": avg_kern_s * 1000.0},
+                     "kernel_ms": avg_kern_s * 1000.0,
+                     "steps_per_launch": steps_per_launch},
+        "issue_roofline": issue,
         "clocks": clk,
         "wall_s_timed": wall,
         "time_to_target": ttt,
@@ -593,7 +688,13 @@ def run_ours(args):
         line["perm_cutoffs"] = perm_cutoffs_vs_flatperm()
         line["autotune"] = autotuned_run(w["tours"])
         line["batched"] = batched_vs_plain(args.batch_tours)
+        line["batched"]["stand_in"] = ("stated config: each of the 96 runs to rel. SE of c_nmax <= 1e-3; "
+                                       "here: %d tours per sequence for every run, time and error reported "
+                                       "per form" % args.batch_tours)
         line["served"] = served_vs_one_at_a_time()
+        line["served"]["stand_in"] = ("stated config: n_max log-uniform in [64,1024], targets 1e-3/1e-4, "
+                                      "60 s of arrivals; here: 150 requests, n_max in [64,256], targets "
+                                      "3e-2/1e-2 (the stated mix needs ~1e2-1e4 GPU-s per request)")
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(args.cpu_seconds)
     print(json.dumps(line), flush=True)
@@ -612,7 +713,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--skip-time-to-target", action="store_true")
-    ap.add_argument("--target-cap-s", type=float, default=20.0)
+    ap.add_argument("--target-cap-s", type=float, default=60.0)
     ap.add_argument("--skip-systems", action="store_true")
     ap.add_argument("--batch-tours", type=int, default=16)
     args = ap.parse_args()

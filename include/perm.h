@@ -329,14 +329,20 @@ int perm_autotune(perm_config *cfg, int64_t probe_tours);
  *
  * cfg: as for perm_create_ex; alg must be PERM_ALG2.  cfg->slots = 0 runs
  * as many walks at once as the buffer holds (sequences beyond that are
- * time-sliced at tour boundaries); an explicit cfg->slots whose scratch
- * exceeds the buffer is rejected with PERM_ESCRATCH.  Starts from empty tables and
+ * time-sliced at tour boundaries); an explicit cfg->slots (clamped to n_seq)
+ * whose scratch exceeds the buffer is rejected with PERM_ESCRATCH.  The run
+ * grows every waiting copy on the walk that made it (no shared copies:
+ * share_copies 0 or -1 both mean that here) and uses the automatic layout;
+ * observables, hash_scale, lanes_per_warp, stack_ring, max_ctas other than 0,
+ * or share_copies > 0, return PERM_EUNSUPPORTED.  Starts from empty tables and
  * grows tours_per_seq tours of each of cfg->n_seq sequences (M = n_seq *
  * tours_per_seq).
  * W_n, S_n, Q_n: caller-owned DEVICE arrays of n_max+1 entries, overwritten
  * with the raw tables at the stored scale (as perm_tables; S_n as uint64).
  * steps: host pointer (may be NULL) for the number of growth steps.
- * stream: a cudaStream_t (NULL = legacy default stream); the call waits for it.
+ * stream: a cudaStream_t (NULL = legacy default stream).  The call is
+ * synchronous: it queues its work on `stream`, waits for that stream, and
+ * returns after the run has finished.
  * Returns PERM_OK, PERM_EINVAL, PERM_EUNSUPPORTED, PERM_ESCRATCH (the requested
  * walks' scratch exceeds the buffer), PERM_EDEVICE, or a kernel status
  * (PERM_EOVERFLOW, PERM_ETIMEOUT).  No cudaMalloc, cudaFree or allocating

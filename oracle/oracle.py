@@ -35,6 +35,7 @@ def configure(L):
     L.orc_create.argtypes = [C.POINTER(C.c_void_p), C.c_int, C.c_int, C.c_int,
                              C.c_uint64, C.c_uint32, C.c_int]
     L.orc_run.argtypes = [C.c_void_p, C.c_int64]
+    L.orc_run_threads.argtypes = [C.c_void_p, C.c_int64, C.c_int]
     L.orc_set_cutoffs.argtypes = [C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_double),
                                   C.c_int, C.c_double]
     dp = C.POINTER(C.c_double)
@@ -139,6 +140,12 @@ class Oracle:
         rc = lib().orc_run(self._h, tours_per_seq)
         if rc != 0:
             raise RuntimeError("orc_run failed: %d" % rc)
+
+    def run_threads(self, tours_per_seq, threads):
+        """Algorithm 2 on `threads` host threads sharing the table (Sec. 3)."""
+        rc = lib().orc_run_threads(self._h, tours_per_seq, threads)
+        if rc != 0:
+            raise RuntimeError("orc_run_threads failed: %d" % rc)
 
     def tables(self):
         ntab = self.n_seq if self.alg == ORC_ALG1 else 1

@@ -66,6 +66,7 @@
 #include "perm_oracle.h"
 
 #include <math.h>
+#include <pthread.h>
 #include <stdlib.h>
 #include <string.h>
 
@@ -595,4 +596,155 @@ int orc_estimates(const orc_state *h, double *log_cn, double *S_n, double *relva
         if (relvar_n) relvar_n[n] = (ok && est > 0.0) ? var / (est * est) : INFINITY;
     }
     return ORC_OK;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Algorithm 2 on several host threads (Sec. 3: the paper ran one flatPERM    */
+/* sequence per thread, every thread reading and updating the shared table W */
+/* as it goes).  This is the CPU baseline of the benchmark; the parity tests */
+/* use the sequential run above, which this section does not touch.  Each    */
+/* thread takes tour tickets g (sequence g mod N, tour g div N) from a shared */
+/* counter, so M counts every tour started by any thread; the tables are     */
+/* updated with atomic adds, and a node reads W_n and M as they are at that  */
+/* moment (the paper's "real time" sharing).  Results depend on the threads' */
+/* interleaving, so only their statistics are reproducible.                  */
+/* ------------------------------------------------------------------------- */
+static void atomic_add_f64(double *p, double v) {
+    uint64_t old_bits = __atomic_load_n((uint64_t *)p, __ATOMIC_RELAXED);
+    for (;;) {
+        double old, sum;
+        memcpy(&old, &old_bits, 8);
+        sum = old + v;
+        uint64_t new_bits;
+        memcpy(&new_bits, &sum, 8);
+        if (__atomic_compare_exchange_n((uint64_t *)p, &old_bits, new_bits, 1, __ATOMIC_RELAXED,
+                                        __ATOMIC_RELAXED))
+            return;
+    }
+}
+
+static double atomic_load_f64(const double *p) {
+    uint64_t bits = __atomic_load_n((const uint64_t *)p, __ATOMIC_RELAXED);
+    double v;
+    memcpy(&v, &bits, 8);
+    return v;
+}
+
+typedef struct {
+    orc_state *h;
+    int64_t last;            /* tickets below this are tours of this call */
+    occset occ;
+    int32_t *coords;
+    stack_rec *stack;
+    double *X;
+    int64_t steps;
+    int rc;
+} mt_worker;
+
+/* One tour on a worker's own walk state against the shared table. */
+static int mt_tour(mt_worker *wk, uint32_t seq, uint32_t tour, int64_t g) {
+    orc_state *h = wk->h;
+    const int d = h->d, n_max = h->n_max;
+    int32_t *co = wk->coords;
+    long sp = 0;
+    int n = 0;
+    double W = 1.0;
+    uint64_t ordinal = 0;
+    for (int i = 0; i < d; ++i) co[i] = 0;
+    wk->occ.n = 0;
+    occ_set(&wk->occ, co, 1);
+    for (;;) {
+        /* the sum of the earlier weights at this length and the tours started so far
+         * (this one included), read as they are now; then accumulate (eq. 4) */
+        double Wsum = atomic_load_f64(&h->Wn[n]);
+        int64_t M = __atomic_load_n(&h->M[0], __ATOMIC_RELAXED);
+        if (M > wk->last) M = wk->last;
+        if (M < g + 1) M = g + 1;
+        atomic_add_f64(&h->Wn[n], W);
+        __atomic_fetch_add(&h->Sn[n], 1, __ATOMIC_RELAXED);
+        wk->X[n] += W;
+        wk->steps += 1;
+        node_out o;
+        int rc = grow_node(d, n_max, n, co + (long)n * d, &wk->occ, W, Wsum, M, ordinal, seq, tour,
+                           h->seed, h->run, NULL, &o);
+        ordinal += 1;
+        if (rc == ORC_CHILDREN) {
+            for (int i = o.c - 1; i >= 1; --i) {
+                if (sp >= h->stack_cap) return ORC_EOVERFLOW;
+                wk->stack[sp].depth = n;
+                wk->stack[sp].dir = o.dirs[i];
+                wk->stack[sp].w = o.child_w;
+                ++sp;
+            }
+            add_step(d, co + (long)n * d, o.dirs[0], co + (long)(n + 1) * d);
+            n += 1;
+            wk->occ.n = n;
+            occ_set(&wk->occ, co + (long)n * d, 1);
+            W = o.child_w;
+            continue;
+        }
+        if (sp == 0) break;
+        --sp;
+        int dp = wk->stack[sp].depth;
+        for (int k = n; k > dp; --k) occ_set(&wk->occ, co + (long)k * d, 0);
+        add_step(d, co + (long)dp * d, wk->stack[sp].dir, co + (long)(dp + 1) * d);
+        n = dp + 1;
+        wk->occ.n = n;
+        occ_set(&wk->occ, co + (long)n * d, 1);
+        W = wk->stack[sp].w;
+    }
+    for (int k = n; k >= 0; --k) occ_set(&wk->occ, co + (long)k * d, 0);
+    wk->occ.n = -1;
+    for (int k = 0; k <= n_max; ++k) {
+        if (wk->X[k] != 0.0) atomic_add_f64(&h->Qn[k], wk->X[k] * wk->X[k]);
+        wk->X[k] = 0.0;
+    }
+    return ORC_OK;
+}
+
+static void *mt_main(void *arg) {
+    mt_worker *wk = (mt_worker *)arg;
+    orc_state *h = wk->h;
+    for (;;) {
+        int64_t g = __atomic_fetch_add(&h->M[0], 1, __ATOMIC_RELAXED);
+        if (g >= wk->last) break;
+        int rc = mt_tour(wk, (uint32_t)(g % h->n_seq), (uint32_t)(g / h->n_seq), g);
+        if (rc != ORC_OK) { wk->rc = rc; break; }
+    }
+    return NULL;
+}
+
+int orc_run_threads(orc_state *h, int64_t tours_per_seq, int threads) {
+    if (!h || tours_per_seq < 0 || threads < 1 || threads > 1024 || h->alg != ORC_ALG2 || h->cut_hi)
+        return ORC_EINVAL;
+    const int64_t first = h->M[0], last = first + tours_per_seq * (int64_t)h->n_seq;
+    mt_worker *wk = (mt_worker *)calloc((size_t)threads, sizeof(mt_worker));
+    pthread_t *tid = (pthread_t *)calloc((size_t)threads, sizeof(pthread_t));
+    int rc = (wk && tid) ? ORC_OK : ORC_ENOMEM;
+    const size_t L = (size_t)h->n_max + 1;
+    for (int t = 0; t < threads && rc == ORC_OK; ++t) {
+        wk[t].h = h;
+        wk[t].last = last;
+        wk[t].coords = (int32_t *)calloc(L * h->d, sizeof(int32_t));
+        wk[t].stack = (stack_rec *)calloc((size_t)h->stack_cap, sizeof(stack_rec));
+        wk[t].X = (double *)calloc(L, sizeof(double));
+        if (!wk[t].coords || !wk[t].stack || !wk[t].X || occ_init(&wk[t].occ, h->d, h->n_max) != ORC_OK)
+            rc = ORC_ENOMEM;
+        wk[t].occ.coords = wk[t].coords;
+    }
+    int started = 0;
+    for (int t = 0; t < threads && rc == ORC_OK; ++t) {
+        if (pthread_create(&tid[t], NULL, mt_main, &wk[t]) != 0) { rc = ORC_ENOMEM; break; }
+        ++started;
+    }
+    for (int t = 0; t < started; ++t) pthread_join(tid[t], NULL);
+    if (started > 0) h->M[0] = last;            /* tickets handed out past the end are void */
+    for (int t = 0; wk && t < threads; ++t) {
+        h->steps += wk[t].steps;
+        if (rc == ORC_OK && wk[t].rc != ORC_OK) rc = wk[t].rc;
+        free(wk[t].coords); free(wk[t].stack); free(wk[t].X); free(wk[t].occ.box);
+    }
+    free(wk); free(tid);
+    h->tours_done[0] = h->M[0];
+    return rc;
 }

@@ -76,6 +76,11 @@ int orc_create(orc_state **out, int d, int n_max, int n_seq, uint64_t seed,
 int orc_set_cutoffs(orc_state *h, const double *T_hi, const double *t_lo, int copies, double q);
 /* Continue the simulation by tours_per_seq tours of every sequence. */
 int orc_run(orc_state *h, int64_t tours_per_seq);
+/* The same on `threads` host threads sharing the table (Sec. 3, Algorithm 2 as
+ * the paper ran it: threads take tour tickets, tables updated atomically and
+ * read as they are at each node).  Algorithm 2 and flatPERM only (ORC_EINVAL
+ * otherwise).  Not reproducible node by node: the interleaving decides. */
+int orc_run_threads(orc_state *h, int64_t tours_per_seq, int threads);
 /* Raw tables (stored scale): W_n, S_n, Q_n over n = 0..n_max (Alg. 2), or the
  * per-sequence rows concatenated (Alg. 1); M (tours started, per sequence for
  * Alg. 1 in M_out[0..N-1]); steps = nodes processed; max stack depth. */

@@ -63,6 +63,12 @@ extern "C" int perm_run_static(const perm_config *cfg, int64_t tours_per_seq, do
     if (cfg->threshold != PERM_THRESH_SNAPSHOT && cfg->threshold != PERM_THRESH_FRESH) return PERM_EINVAL;
     if (cfg->slots < 0 || cfg->refresh_ns < 0 || !(cfg->max_seconds >= 0.0)) return PERM_EINVAL;
     if (!(cfg->ramp_gamma >= 0.0) || cfg->ramp_gamma > 1e6) return PERM_EINVAL;
+    // settings this entry point does not carry out are refused, not ignored: the
+    // eq. 5 sums, a chosen layout (walks per warp, hash size, stack ring, CTA cap)
+    // and shared copies (the run grows every copy on the walk that made it)
+    if (cfg->observables != 0 || cfg->hash_scale != 0 || cfg->lanes_per_warp != 0 ||
+        cfg->stack_ring != 0 || cfg->max_ctas != 0 || cfg->share_copies > 0)
+        return PERM_EUNSUPPORTED;
     const bool key64 = (d == 3 && n_max > 512);
     if (n_max > (d == 2 ? 32766 : (key64 ? (1 << 20) - 2 : 512))) return PERM_EUNSUPPORTED;
     cudaStream_t st = (cudaStream_t)stream;
@@ -73,15 +79,20 @@ extern "C" int perm_run_static(const perm_config *cfg, int64_t tours_per_seq, do
     const size_t per_slot = L * sizeof(double) + (size_t)n_max * (sizeof(uint32_t) + sizeof(double));
     if (counters + 3 * 256 + per_slot > PERM_STATIC_SCRATCH_BYTES) return PERM_ESCRATCH;
     const long long fit = (long long)((PERM_STATIC_SCRATCH_BYTES - counters - 3 * 256) / per_slot);
-    if (cfg->slots > 0 && cfg->slots > fit) return PERM_ESCRATCH;
+    // an explicit walk count beyond the sequences is clamped first (one walk per
+    // sequence at most), then checked against what the buffer holds
+    const long long asked = cfg->slots > n_seq ? n_seq : cfg->slots;
+    if (asked > 0 && asked > fit) return PERM_ESCRATCH;
 
     void *base = nullptr;
     int rc = scratch_address(&base);
     if (rc != PERM_OK) return rc;
-    int dev = 0;
-    cudaDeviceProp prop;
-    if (cudaGetDevice(&dev) != cudaSuccess || cudaGetDeviceProperties(&prop, dev) != cudaSuccess)
+    int dev = 0, smem_optin = 0, num_sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&num_sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
         return PERM_EDEVICE;
+    const size_t optin = (size_t)smem_optin;
 
     // layout: one walk per thread, 32 walks per warp at most, as many warps per
     // CTA as shared memory allows, one CTA per SM
@@ -94,18 +105,18 @@ extern "C" int perm_run_static(const perm_config *cfg, int64_t tours_per_seq, do
     for (;; stride /= 2) {
         head = perm::cta_smem_bytes(d, key64, n_max, log2h, K, 0, snap, stride);
         per_warp = perm::cta_smem_bytes(d, key64, n_max, log2h, K, 1, snap, stride) - head;
-        if (head + per_warp <= prop.sharedMemPerBlockOptin || stride == 1) break;
+        if (head + per_warp <= optin || stride == 1) break;
     }
-    if (head + per_warp > prop.sharedMemPerBlockOptin) return PERM_EUNSUPPORTED;
-    int max_warps = (int)((prop.sharedMemPerBlockOptin - head) / per_warp);
+    if (head + per_warp > optin) return PERM_EUNSUPPORTED;
+    int max_warps = (int)((optin - head) / per_warp);
     if (max_warps > 4) max_warps = 4;
 
     long long slots = cfg->slots ? cfg->slots : n_seq;
     if (slots > n_seq) slots = n_seq;
     if (slots > fit) slots = fit;
-    const long long cap = (long long)prop.multiProcessorCount * max_warps * stride;
+    const long long cap = (long long)num_sms * max_warps * stride;
     if (slots > cap) slots = cap;
-    const long long per_cta = (slots + prop.multiProcessorCount - 1) / prop.multiProcessorCount;
+    const long long per_cta = (slots + num_sms - 1) / num_sms;
     int warps = (int)((per_cta + stride - 1) / stride);
     if (warps > max_warps) warps = max_warps;
     if (warps < 1) warps = 1;
@@ -157,9 +168,12 @@ extern "C" int perm_run_static(const perm_config *cfg, int64_t tours_per_seq, do
     if (e != cudaSuccess) return PERM_EDEVICE;
     e = perm::launch_finalize(P.tickets, P.tour_limit, st);
     if (e != cudaSuccess) return PERM_EDEVICE;
-    if (cudaStreamSynchronize(st) != cudaSuccess) return PERM_EDEVICE;
+    // the counters come back on the caller's stream, which is then waited for (no
+    // blocking copy on the legacy default stream, which would wait for every stream)
     unsigned long long host_cnt[8];
-    if (cudaMemcpy(host_cnt, cnt, sizeof(host_cnt), cudaMemcpyDeviceToHost) != cudaSuccess) return PERM_EDEVICE;
+    if (cudaMemcpyAsync(host_cnt, cnt, sizeof(host_cnt), cudaMemcpyDeviceToHost, st) != cudaSuccess)
+        return PERM_EDEVICE;
+    if (cudaStreamSynchronize(st) != cudaSuccess) return PERM_EDEVICE;
     if (steps) *steps = (int64_t)host_cnt[1];
     int status = 0;
     std::memcpy(&status, &host_cnt[7], sizeof(int));

@@ -43,6 +43,7 @@ class Request:
     steps: int = 0
     rel_se: float = float("inf")
     log_cn: np.ndarray = None
+    relvar: np.ndarray = None     # relative variance of every c_n, when the engine gives it
     met: bool = False
 
 
@@ -89,6 +90,7 @@ class Server:
             req.tours += req.chunk_tours
             log_cn, rel_se, steps = self.engine.read(job)
             req.log_cn, req.rel_se, req.steps = log_cn, rel_se, steps
+            req.relvar = getattr(job, "relvar", None)
             if rel_se <= req.target or req.tours >= req.max_tours:
                 req.met = rel_se <= req.target
                 req.retired = self.now()
@@ -171,6 +173,7 @@ class GpuEngine:
 
     def read(self, job):
         lc, S, rv = job.run.estimates()
+        job.relvar = rv
         n_max = job.run.n_max
         st = job.run.stats()
         if st["status"] != 0:

@@ -104,3 +104,38 @@ def test_served_results_equal_alone():
         fin = np.isfinite(lc)
         assert np.allclose(r.log_cn[fin], lc[fin], rtol=0, atol=1e-12)
         assert math.isclose(math.sqrt(rv[r.n_max]), r.rel_se, rel_tol=1e-9)
+
+
+def test_served_interacting_requests_meet_exact_counts_and_the_oracle(exact_counts):
+    """A burst of interacting requests served together as the benchmark serves
+    them (snapshot thresholds, 512-1024 sequences each, continuous batching on
+    densely packed CTAs), at lengths where c_n is known exactly (n_max 16 on the
+    square lattice, 11 on the cubic).  Every retired request meets its target,
+    its estimates agree with exact c_n (Sec. 1, eq. 3) within 4.5 standard errors
+    at every length, and with an independent run of the CPU oracle within 4.5
+    combined standard errors."""
+    from oracle import oracle as orc
+    torch_cuda()
+    reqs = []
+    for i in range(12):
+        d = 2 + i % 2
+        reqs.append(ps.Request(rid=i, d=d, n_max=16 if d == 2 else 11, target=5e-3,
+                               arrival=0.003 * i, n_seq=512 if i % 3 else 1024, seed=200 + i,
+                               chunk_tours=4, max_tours=2000))
+    srv = ps.Server(ps.GpuEngine(max_ctas=-1), hbm_budget_bytes=120e9, max_resident=8)
+    done = srv.serve(reqs)
+    assert len(done) == 12 and all(r.met for r in done)
+    assert srv.peak_resident >= 2
+    ref = {}
+    for d, n_max in ((2, 16), (3, 11)):
+        o = orc.Oracle(d, n_max, 12, seed=4242)
+        o.run(3000)
+        lc, S, rv = o.estimates()
+        ref[d] = (lc, rv)
+    for r in done:
+        lc, rv = r.log_cn, r.relvar
+        z = zscores(lc, rv, exact_counts[r.d][: r.n_max + 1])
+        assert np.all(np.abs(z[2:]) < 4.5), (r.rid, z)
+        lco, rvo = ref[r.d]
+        zo = (lc - lco)[2:] / np.sqrt(rv[2:] + rvo[2:] + 1e-10)
+        assert np.all(np.abs(zo) < 4.5), (r.rid, zo)

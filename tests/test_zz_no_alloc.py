@@ -12,12 +12,14 @@ whole-run tests applies: counts exact, weights to relative 1e-12.
 This file is collected last on purpose.  If it fails, a run that stops at the
 first failure has already run every other test.
 """
+import math
+
 import numpy as np
 import pytest
 
 import paper_2002_03000_gb300 as pg
 from paper_2002_03000_gb300 import _native as nat
-from tests.gpu_util import torch_cuda
+from tests.gpu_util import torch_cuda, zscores
 
 pytestmark = pytest.mark.gpu
 
@@ -32,9 +34,10 @@ def _reference(d, n_max, n_seq, seed, tours):
     return t, steps
 
 
-def _static(torch, d, n_max, n_seq, seed, tours):
+def _static(torch, d, n_max, n_seq, seed, tours, threshold=pg.PERM_THRESH_FRESH, slots=0):
     cfg = nat.perm_config_init(d, n_max, n_seq, seed)
-    cfg.threshold = pg.PERM_THRESH_FRESH
+    cfg.threshold = threshold
+    cfg.slots = slots
     cfg.max_seconds = 120.0
     L = n_max + 1
     # fill the outputs with garbage first: the call must overwrite them
@@ -77,3 +80,55 @@ def test_static_run_rejects_oversized_request():
         nat.perm_run_static(cfg, 1, W.data_ptr(), S.data_ptr(), Q.data_ptr())
     assert e.value.code == nat.PERM_ESCRATCH
     assert "static buffer" in nat.strerror(nat.PERM_ESCRATCH)
+
+
+def test_static_interacting_sequences_obey_the_counting_theorem(exact_counts):
+    """Snapshot thresholds, a few hundred interacting sequences (the static
+    layout: up to 4 warps of 32 walks per CTA, a refresher warp per CTA), two
+    calls in a row: every tour passes lengths 0 and 1 once (S_0 = S_1 = M,
+    c_1 = 2d exactly) and the estimates meet exact c_n (Sec. 1, eq. 3) within
+    4.5 standard errors at every length."""
+    torch = torch_cuda()
+    for d, n_max, N, tours, seed in [(2, 16, 300, 40, 0x5EED), (3, 11, 400, 30, 0xFEED)]:
+        for _ in range(2):
+            got, steps = _static(torch, d, n_max, N, seed, tours, threshold=pg.PERM_THRESH_SNAPSHOT)
+            M = N * tours
+            assert got["S"][0] == M and got["S"][1] == M
+            lc, rv = nat.perm_estimates_from_tables(d, n_max, got["W"], got["Q"], [M])
+            assert math.isclose(math.exp(lc[1]), 2 * d, rel_tol=1e-12)
+            z = zscores(lc, rv, exact_counts[d][: n_max + 1])
+            assert np.all(np.abs(z[2:]) < 4.5), (d, z)
+            assert steps == int(got["S"].sum())
+
+
+def test_static_walks_limited_by_the_buffer():
+    """More sequences than the buffer holds walks for (8192 of length 256 need
+    about 42 MB of tour sums and spill areas): with slots = 0 the run takes
+    what fits, time-slices the rest at tour boundaries and completes."""
+    torch = torch_cuda()
+    d, n_max, N, tours = 2, 256, 8192, 2
+    per_walk = (n_max + 1) * 8 + n_max * 12
+    assert N * per_walk > nat.PERM_STATIC_SCRATCH_BYTES
+    got, steps = _static(torch, d, n_max, N, 0xC0DE, tours, threshold=pg.PERM_THRESH_SNAPSHOT)
+    assert got["S"][0] == N * tours and got["S"][1] == N * tours
+    assert steps == int(got["S"].sum())
+
+
+def test_static_run_refuses_settings_it_does_not_carry_out():
+    torch = torch_cuda()
+    L = 17
+    W = torch.zeros(L, dtype=torch.float64, device="cuda")
+    S = torch.zeros(L, dtype=torch.int64, device="cuda")
+    Q = torch.zeros(L, dtype=torch.float64, device="cuda")
+    for field, value in (("observables", 1), ("hash_scale", 1), ("lanes_per_warp", 4),
+                         ("stack_ring", 64), ("max_ctas", 8), ("share_copies", 4)):
+        cfg = nat.perm_config_init(2, 16, 4, 1)
+        setattr(cfg, field, value)
+        with pytest.raises(nat.PermError) as e:
+            nat.perm_run_static(cfg, 1, W.data_ptr(), S.data_ptr(), Q.data_ptr())
+        assert e.value.code == nat.PERM_EUNSUPPORTED, field
+    # an explicit walk count above the sequences is clamped to them, not refused
+    cfg = nat.perm_config_init(2, 16, 1, 1)
+    cfg.slots = 4096
+    nat.perm_run_static(cfg, 3, W.data_ptr(), S.data_ptr(), Q.data_ptr())
+    assert S.cpu().numpy()[0] == 3
