@@ -34,8 +34,8 @@ MUTATIONS = {
     "survival with probability 1 - r": ("if (!(u0 < r)) return ORC_LEAF_PRUNED;",
                                         "if (!(u0 < 1.0 - r)) return ORC_LEAF_PRUNED;"),
     "Fisher-Yates offset dropped": ("int j = i + (int)(prod >> 32);", "int j = (int)(prod >> 32);"),
-    "backtrack leaves a site": ("for (int k = n; k > dp; --k) occ_set",
-                                "for (int k = n; k > dp + 1; --k) occ_set"),
+    "backtrack leaves a site": ("for (int k = n; k > dp; --k) occ_set(&h->occ",
+                                "for (int k = n; k > dp + 1; --k) occ_set(&h->occ"),
     "variance from X not X^2": ("Qn[k] += h->X[k] * h->X[k];", "Qn[k] += h->X[k];"),
     "direction signs swapped": ("to[j >> 1] += (j & 1) ? -1 : 1;", "to[j >> 1] += (j & 1) ? 1 : -1;"),
     "scale step wrong": ("int dE = orc_scale_exp(d, n + 1) - orc_scale_exp(d, n);",
