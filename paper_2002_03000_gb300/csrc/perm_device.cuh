@@ -172,12 +172,15 @@ __device__ __forceinline__ int probe_neighbours(const Key *tab, int S, int lane,
 //
 // The estimate: x = M / (1 + Wsum/W), with the two doubles entering through
 // their mantissas rounded to 24 bits (nearest, ties to even; a carry bumps the
-// exponent) and their exponents, and every operation a correctly rounded
-// single-precision one.  Six roundings of relative size <= 2^-24 (the two
-// mantissas, the quotient, the sum 1 + rho, M and the final quotient) and the
-// three roundings of the double-precision r (<= 4 2^-53) give
-// |x - r| <= 6.01 2^-24 x; every margin below allows 7.02 2^-24 x.  Doubles
-// with no such bound (W zero, negative, subnormal or not finite; Wsum
+// exponent) and their exponents.  Each quotient is a product with the
+// hardware's approximate reciprocal (rcp.approx, at most one unit in the last
+// place, i.e. relative error <= 2^-23) rounded once more; the other operations
+// are correctly rounded single-precision ones.  Relative errors: the two
+// mantissas 2^-24 each, the quotient 3 2^-24, the sum 1 + rho 2^-24 (plus rho's
+// own 5 2^-24 scaled by rho/(1 + rho) < 1), M 2^-24 and the final quotient
+// 3 2^-24, with the three roundings of the double-precision r (<= 4 2^-53):
+// |x - r| <= 10.02 2^-24 x.  Every margin below allows at least 15 2^-24 x.
+// Doubles with no such bound (W zero, negative, subnormal or not finite; Wsum
 // negative, subnormal or not finite; Wsum/W above 2^100) set `odd` and take
 // the exact path.
 // ---------------------------------------------------------------------------
@@ -190,6 +193,13 @@ __device__ __forceinline__ uint32_t mant24_bits(unsigned long long b, int &ef) {
     return (127u << 23) | keep;
 }
 
+// 1/v to within one unit in the last place (v normal and positive).
+__device__ __forceinline__ float rcp_approx(float v) {
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(v));
+    return r;
+}
+
 __device__ __forceinline__ float ratio_estimate(double W, double Wsum, unsigned long long M, bool &odd) {
     const unsigned long long wb = (unsigned long long)__double_as_longlong(W);
     const unsigned long long sb = (unsigned long long)__double_as_longlong(Wsum);
@@ -199,7 +209,7 @@ __device__ __forceinline__ float ratio_estimate(double W, double Wsum, unsigned 
                (es == 0 && !s_zero);
     const float mw = __uint_as_float(mant24_bits(wb, ew));
     const float ms = __uint_as_float(mant24_bits(sb, es));
-    const float q = __fdiv_rn(ms, mw);               // in (0.5, 2)
+    const float q = __fmul_rn(ms, rcp_approx(mw));    // in (0.5, 2)
     int e = es - ew;
     bad = bad || (!s_zero && e > 100);
     // below 2^-100 the ratio only moves 1 + rho by less than 2^-99
@@ -209,7 +219,7 @@ __device__ __forceinline__ float ratio_estimate(double W, double Wsum, unsigned 
     const float s = __fadd_rn(1.0f, rho);
     const float Mf = (M >> 32) ? __ull2float_rn(M) : __uint2float_rn((uint32_t)M);
     odd = bad;
-    return __fdiv_rn(Mf, s);
+    return __fmul_rn(Mf, rcp_approx(s));
 }
 
 // r exactly as defined, in double precision: three correctly rounded operations
@@ -243,7 +253,7 @@ __device__ __forceinline__ double widen(float f) {
 //  - floor and ceil: x farther than x 2^-20 from an integer gives
 //    floor r = floor x;
 //  - the u0 comparisons, on w0 against the threshold P = (ceil x - x) 2^32 or
-//    P = x 2^32 (exact in single precision), which is within 1797 x of the
+//    P = x 2^32 (exact in single precision), which is within 2565 x of the
 //    threshold of r: |w0 - P| > 4096 x + 512 settles them (the 512 covers the
 //    rounding of w0 to single precision and of the difference, 128 each).
 // Returns c (0: pruned); `surv` marks a survivor of pruning.

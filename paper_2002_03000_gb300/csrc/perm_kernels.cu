@@ -9,12 +9,13 @@
 // the tree of copies made by enrichment (Sec. 2).
 //
 // Threshold sources for Algorithm 2 (one shared table W, Fig. 1):
-//  - snapshot: every CTA accumulates W_n and S_n into shared-memory deltas; one
-//    extra warp per CTA flushes them to the global table every refresh period
-//    and reloads a shared-memory copy of [W_n] = W_n/M.  The nodes read that
-//    copy (a stale but fixed threshold keeps the estimator unbiased: enrichment
-//    and pruning conserve the expected weight for any r).  Walks with no tour to
-//    start grow waiting copies of other walks' tours (shared copies).
+//  - snapshot: every node adds its weight to the global table with a
+//    reduction that returns nothing; one extra warp per CTA reloads a
+//    shared-memory copy of W_n and M every refresh period.  The nodes read
+//    that copy (a stale but fixed threshold keeps the estimator unbiased:
+//    enrichment and pruning conserve the expected weight for any r).  Walks
+//    with no tour to start grow waiting copies of other walks' tours (shared
+//    copies).
 //  - fresh: every node adds its weight to the global table with an atomic that
 //    returns the previous sum, and uses it at once (sequential flatPERM exactly
 //    when one walk runs).
@@ -34,6 +35,7 @@ namespace {
 
 constexpr int kStride = 32;        // interleave stride of the snapshot-state kernel
 constexpr int kUnwind = 8;         // hash deletions per walk per iteration
+constexpr int kNodePasses = 2;     // nodes a walk may grow per iteration
 constexpr int kPoolExtra = 4;      // extra tour tickets fetched per warp (snapshot)
 constexpr int kChunk = 8;          // stack records moved per spill or fill (ring >= 2 kChunk)
 constexpr unsigned kRowFree = 0xFFFFFFFFu;   // outst: the walk's tour-sum row is unused
@@ -88,7 +90,7 @@ __host__ __device__ __forceinline__ size_t warp_region_bytes(int n_max, int log2
 __host__ __device__ __forceinline__ size_t head_region_bytes(int n_max, bool snapshot) {
     const size_t L = (size_t)n_max + 1;
     size_t b = 64 + 2 * 64 * 8;   // header + two a/c tables
-    if (snapshot) b += 8 * L + 8 * L + (((4 * L) + 15) & ~(size_t)15);
+    if (snapshot) b += 8 * L;     // the snapshot of W_n
     return (b + 15) & ~(size_t)15;
 }
 
@@ -250,12 +252,8 @@ __device__ __forceinline__ void grow_run(const RunDev &P, unsigned char *smem, c
     double *aoc = reinterpret_cast<double *>(smem + 64);
     unsigned char *p = smem + 64 + 1024;
     double *Wsnap = nullptr;
-    double *Wd = nullptr;
-    unsigned int *Sd = nullptr;
     if (snapshot) {
         Wsnap = reinterpret_cast<double *>(p); p += 8 * (size_t)L;
-        Wd = reinterpret_cast<double *>(p); p += 8 * (size_t)L;
-        Sd = reinterpret_cast<unsigned int *>(p); p += align16(4 * (size_t)L);
     }
     const int ST = P.stride;
     const size_t wbytes = warp_region_bytes(P.n_max, P.log2h, K, sizeof(Key), ST);
@@ -276,7 +274,7 @@ __device__ __forceinline__ void grow_run(const RunDev &P, unsigned char *smem, c
     __syncthreads();
 
     // ----------------------------------------------------------------------
-    // refresher warp (snapshot form): flush the CTA's deltas, reload [W_n]
+    // refresher warp (snapshot form): reload the snapshot of W_n and M
     // ----------------------------------------------------------------------
     if (snapshot && warp == P.worker_warps) {
         const long long t0 = global_ns();
@@ -286,16 +284,6 @@ __device__ __forceinline__ void grow_run(const RunDev &P, unsigned char *smem, c
         for (long long it = 0;; ++it) {
             const int done = __shfl_sync(kFull, *(volatile int *)&head->done_warps, 0);
             __threadfence_block();
-            // W_n deltas feed the thresholds and go out every period; the
-            // sample counts S_n are only read after the launch
-            for (int k = lane; k < L; k += 32) {
-                const double wv = __longlong_as_double((long long)atomicExch(reinterpret_cast<unsigned long long *>(&Wd[k]), 0ull));
-                if (wv != 0.0) atomicAdd(&P.Wn[k], wv);
-                if (done >= P.worker_warps) {
-                    const unsigned int sv = atomicExch(&Sd[k], 0u);
-                    if (sv) atomicAdd(&P.Sn[k], (unsigned long long)sv);
-                }
-            }
             if (done >= P.worker_warps) {
                 if (lane == 0) atomicAdd(P.refreshes, (unsigned long long)it);
                 break;
@@ -625,7 +613,12 @@ __device__ __forceinline__ void grow_run(const RunDev &P, unsigned char *smem, c
             idle_ns = 500u;
         }
 
-        // ---------------- one node ----------------
+        // ---------------- nodes: up to kNodePasses per iteration ----------------
+        // A walk whose node made children grows its next node in the same
+        // iteration, so that the warp-wide parts of the loop are shared by more
+        // nodes; a walk that reached a leaf waits for the backtrack below.
+        for (int pass = 0; pass < kNodePasses; ++pass) {
+        if (pass > 0 && !__any_sync(kFull, state == kNode)) break;
         if (state == kNode) {
             // the sum of the weights recorded at this length before the node (a
             // snapshot, or the global table's value returned by the node's own add)
@@ -633,8 +626,9 @@ __device__ __forceinline__ void grow_run(const RunDev &P, unsigned char *smem, c
             double Wsum;
             unsigned long long Mb;
             if (snapshot) {
-                atomicAdd(&Wd[n], W);
-                atomicAdd(&Sd[n], 1u);
+                // fire-and-forget reductions into the global table (no value comes back)
+                atomicAdd(P.Wn + n, W);
+                atomicAdd(P.Sn + n, 1ull);
                 Wsum = *(volatile double *)&Wsnap[n];
                 const unsigned long long Ms = *(volatile unsigned long long *)&head->Ms;
                 Mb = Ms > g + 1ull ? Ms : g + 1ull;
@@ -818,6 +812,7 @@ __device__ __forceinline__ void grow_run(const RunDev &P, unsigned char *smem, c
                 }
                 state = kUnwindState;
             }
+        }
         }
 
         // ---------------- backtrack: LIFO deletions, then resume ----------------
