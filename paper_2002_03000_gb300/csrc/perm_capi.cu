@@ -29,6 +29,7 @@ struct perm_run_s {
     int log2h = 0, slots = 0, ctas = 0, worker_warps = 0, lanes = 0, stride = 32, stack_cache = 16;
     size_t smem = 0;
     int ntab = 1;
+    int xrows = 0;                 // tour-sum rows: one per walk, two with shared copies
     // device buffers
     double *Wn = nullptr, *Qn = nullptr, *X = nullptr, *gstk_w = nullptr, *Rn = nullptr;
     unsigned long long *Sn = nullptr, *tickets = nullptr, *seq_M = nullptr;
@@ -288,7 +289,9 @@ int create_impl(perm_handle *out, const perm_config *cfg, const ForcedLayout *fo
     if (rc == PERM_OK && cfg->observables) rc = dalloc(h, &h->Rn, L * h->ntab);
     if (rc == PERM_OK) rc = dalloc(h, &h->tickets, 1);
     if (rc == PERM_OK) rc = dalloc(h, &h->seq_M, (size_t)n_seq);
-    if (rc == PERM_OK) rc = dalloc(h, &h->X, L * (size_t)h->slots);
+    h->share = cfg->share_copies >= 0 && cfg->alg == PERM_ALG2 && h->thresh == perm::kSnapshot;
+    h->xrows = h->slots * (h->share ? 2 : 1);
+    if (rc == PERM_OK) rc = dalloc(h, &h->X, L * (size_t)h->xrows);
     if (rc == PERM_OK) rc = dalloc(h, &h->gstk_meta, (size_t)n_max * h->slots);
     if (rc == PERM_OK) rc = dalloc(h, &h->gstk_w, (size_t)n_max * h->slots);
     if (rc == PERM_OK) rc = dalloc(h, &h->steps, 1);
@@ -302,7 +305,6 @@ int create_impl(perm_handle *out, const perm_config *cfg, const ForcedLayout *fo
     if (rc == PERM_OK) rc = dalloc(h, &h->status, 1);
     // shared copies: a ring of cells, each one waiting copy record plus the keys of the
     // walk up to its branch point
-    h->share = cfg->share_copies >= 0 && cfg->alg == PERM_ALG2 && h->thresh == perm::kSnapshot;
     h->share_cap = cfg->share_copies > 0 ? cfg->share_copies : kDefaultShareCap;
     if (rc == PERM_OK && h->share) {
         int lc = 6;
@@ -315,9 +317,9 @@ int create_impl(perm_handle *out, const perm_config *cfg, const ForcedLayout *fo
         if (rc == PERM_OK) rc = dalloc(h, &h->dq_free, cap);
         if (rc == PERM_OK) rc = dalloc(h, &h->dq_head, 1);
         if (rc == PERM_OK) rc = dalloc(h, &h->dq_tail, 1);
-        if (rc == PERM_OK) rc = dalloc(h, &h->outst, (size_t)h->slots);
-        if (rc == PERM_OK) rc = to_code(cudaMemsetAsync(h->outst, 0xFF, sizeof(unsigned int) * h->slots, h->stream));
-        if (rc == PERM_OK) rc = dalloc(h, &h->tmaxn, (size_t)h->slots);
+        if (rc == PERM_OK) rc = dalloc(h, &h->outst, (size_t)h->xrows);
+        if (rc == PERM_OK) rc = to_code(cudaMemsetAsync(h->outst, 0xFF, sizeof(unsigned int) * h->xrows, h->stream));
+        if (rc == PERM_OK) rc = dalloc(h, &h->tmaxn, (size_t)h->xrows);
         if (rc == PERM_OK) rc = dalloc(h, &h->hungry, 1);
     }
     if (rc == PERM_OK) rc = to_code(cudaStreamSynchronize(h->stream));
@@ -510,7 +512,7 @@ int perm_reset(perm_handle h) {
     if (e == cudaSuccess) e = cudaMemsetAsync(h->max_stack, 0, sizeof(unsigned long long), h->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(h->status, 0, sizeof(int), h->stream);
     if (e == cudaSuccess && h->last_status != PERM_OK)   // a stopped run may leave tour sums behind
-        e = cudaMemsetAsync(h->X, 0, L * (size_t)h->slots * sizeof(double), h->stream);
+        e = cudaMemsetAsync(h->X, 0, L * (size_t)h->xrows * sizeof(double), h->stream);
     if (e == cudaSuccess && h->share) {
         const size_t cap = (size_t)1 << h->dq_log2cap;
         e = cudaMemsetAsync(h->dq_head, 0, sizeof(unsigned long long), h->stream);
@@ -518,8 +520,8 @@ int perm_reset(perm_handle h) {
         if (e == cudaSuccess) e = cudaMemsetAsync(h->dq_ready, 0, sizeof(unsigned int) * cap, h->stream);
         if (e == cudaSuccess) e = cudaMemsetAsync(h->dq_free, 0, sizeof(unsigned int) * cap, h->stream);
         if (e == cudaSuccess) e = cudaMemsetAsync(h->hungry, 0, sizeof(int), h->stream);
-        if (e == cudaSuccess) e = cudaMemsetAsync(h->outst, 0xFF, sizeof(unsigned int) * h->slots, h->stream);
-        if (e == cudaSuccess) e = cudaMemsetAsync(h->tmaxn, 0, sizeof(unsigned int) * h->slots, h->stream);
+        if (e == cudaSuccess) e = cudaMemsetAsync(h->outst, 0xFF, sizeof(unsigned int) * h->xrows, h->stream);
+        if (e == cudaSuccess) e = cudaMemsetAsync(h->tmaxn, 0, sizeof(unsigned int) * h->xrows, h->stream);
     }
     if (e != cudaSuccess) return to_code(e);
     h->tour_limit = 0;
@@ -746,7 +748,7 @@ int member_reset(perm_handle h) {
     int rc = perm_reset(h);
     if (rc != PERM_OK) return rc;
     const size_t L = (size_t)h->cfg.n_max + 1;
-    return to_code(cudaMemsetAsync(h->X, 0, L * (size_t)h->slots * sizeof(double), h->stream));
+    return to_code(cudaMemsetAsync(h->X, 0, L * (size_t)h->xrows * sizeof(double), h->stream));
 }
 
 }  // namespace perm

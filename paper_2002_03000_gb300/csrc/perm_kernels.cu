@@ -372,12 +372,16 @@ __device__ __forceinline__ void grow_run(const RunDev &P, unsigned char *smem, c
     long long seq_t = 0;
     unsigned long long pool_lo = 0ull, pool_hi = 0ull;
     bool waiting = false;
+    // tour-sum rows: with shared copies a walk has two, so that it can start its
+    // next tour while parts of its last one still grow on other walks
+    const int rows_per_walk = P.share ? 2 : 1;
+    int myrow = sidx * rows_per_walk;
     // shared copies: the walk grows either its own tour or a part of another
-    // walk's tour (own = that walk's slot, did = the part's donation id)
-    int own = sidx, bot = 0;
+    // walk's tour (own = that tour's row, did = the part's donation id)
+    int own = myrow, bot = 0;
     uint32_t did = 0u;
     bool donated = false;      // a part of this walk's own tour went to another walk
-    bool xbusy = false;        // this walk's tour-sum row is still used by such a part
+    bool xbusy = false;        // every tour-sum row of this walk is still used by such parts
     bool exhausted = bl != nullptr && bl->helper;   // no tour tickets left (a helper takes none)
     int my_hungry = 0;         // lane 0: this warp's share of P.hungry
     unsigned idle_ns = 500u;   // back-off of a warp with nothing to grow
@@ -400,7 +404,13 @@ __device__ __forceinline__ void grow_run(const RunDev &P, unsigned char *smem, c
         // (the whole warp leaves together: one lane's read decides)
         if (bl != nullptr && (iter & 255) == 0 && __shfl_sync(kFull, *(volatile int *)P.status, 0) != 0) break;
         // ---------------- tour tickets ----------------
-        if (state == kNeed && xbusy && *(volatile unsigned int *)(P.outst + sidx) == kRowFree) xbusy = false;
+        if (state == kNeed && xbusy) {
+            if (*(volatile unsigned int *)(P.outst + myrow) == kRowFree) xbusy = false;
+            else if (rows_per_walk == 2 && *(volatile unsigned int *)(P.outst + (myrow ^ 1)) == kRowFree) {
+                myrow ^= 1;
+                xbusy = false;
+            }
+        }
         const bool want_t = state == kNeed && !xbusy && !exhausted;
         const unsigned need = __ballot_sync(kFull, want_t);
         if (need) {
@@ -492,7 +502,7 @@ __device__ __forceinline__ void grow_run(const RunDev &P, unsigned char *smem, c
                 // start a tour at the empty walk (Sec. 1: W(empty) = 1)
                 n = 0; cx = cy = cz = 0; maxn = 0; W = 1.0; ordinal = 0ull;
                 top = 0; sbase = 0; bot = 0;
-                own = sidx; did = 0u; donated = false;
+                own = myrow; did = 0u; donated = false;
                 const int s0 = hash_insert<Key>(hash, ST, lane, P.log2h,
                                                 KeyCodec<D, Key>::encode(0, 0, 0));
                 if (s0 < 0) { set_status(P.status, PERM_EOVERFLOW); state = kDone; }
@@ -743,7 +753,7 @@ __device__ __forceinline__ void grow_run(const RunDev &P, unsigned char *smem, c
                             if (atomicCAS(P.dq_tail, t0, t0 + 1ull) == t0) { pos = t0; got = true; break; }
                         }
                         if (got) {
-                            if (did == 0u && !donated) { P.outst[sidx] = 2u; donated = true; }
+                            if (did == 0u && !donated) { P.outst[own] = 2u; donated = true; }
                             else atomicAdd(P.outst + own, 1u);
                             const uint32_t cell = (uint32_t)pos & dq_mask;
                             unsigned char *cb = P.dq_cells + (size_t)cell * (size_t)P.dq_cell_bytes;
@@ -847,7 +857,7 @@ __device__ __forceinline__ void grow_run(const RunDev &P, unsigned char *smem, c
             if (state == kFlush) {
                 if (did == 0u && !donated) {
                     // the whole tour grew on this walk
-                    frow = sidx; fmaxn = maxn; do_flush = true; shared_flush = false;
+                    frow = own; fmaxn = maxn; do_flush = true; shared_flush = false;
                 } else {
                     // parts of the tour grew elsewhere: the last part to end flushes
                     const unsigned om = atomicMax(P.tmaxn + own, (unsigned)maxn);
@@ -857,7 +867,12 @@ __device__ __forceinline__ void grow_run(const RunDev &P, unsigned char *smem, c
                     shared_flush = true;
                     frow = own;
                     fmaxn = (int)(om > (unsigned)maxn ? om : (unsigned)maxn);
-                    if (!do_flush && did == 0u) xbusy = true;
+                    if (!do_flush && did == 0u) {
+                        // the row stays with the parts still growing: the next tour
+                        // takes the walk's other row, if that one is free
+                        myrow ^= rows_per_walk - 1;
+                        xbusy = *(volatile unsigned int *)(P.outst + myrow) != kRowFree;
+                    }
                 }
             }
             unsigned fm = __ballot_sync(kFull, state == kFlush && do_flush);
@@ -904,7 +919,7 @@ __device__ __forceinline__ void grow_run(const RunDev &P, unsigned char *smem, c
                         P.seq_M[cur_seq] = (unsigned long long)seq_t;
                     }
                 }
-                own = sidx; did = 0u; donated = false; do_flush = false;
+                own = myrow; did = 0u; donated = false; do_flush = false;
                 state = kNeed;
             }
         }

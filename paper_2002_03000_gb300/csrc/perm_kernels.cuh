@@ -40,7 +40,8 @@ struct RunDev {
     unsigned long long *tickets;   // Alg. 2: tours started (M); Alg. 1: next sequence
     unsigned long long *seq_M;     // Alg. 1: tours done per sequence
     // per-walk scratch
-    double *X;                     // slots x (n_max+1): this tour's weight per length
+    double *X;                     // tour-sum rows x (n_max+1): a tour's weight per length
+                                   // (rows: one per walk; two with shared copies)
     uint32_t *gstk_meta;           // slots x n_max
     double *gstk_w;                // slots x n_max
     // statistics and status
@@ -65,8 +66,8 @@ struct RunDev {
     unsigned long long *dq_tail;   // donations reserved
     unsigned int *dq_ready;        // per cell: round + 1 once written for that round
     unsigned int *dq_free;         // per cell: first round that may write it
-    unsigned int *outst;           // per walk: live parts of its tour (kRowFree: row unused)
-    unsigned int *tmaxn;           // per walk: deepest length over the parts of its tour
+    unsigned int *outst;           // per tour-sum row: live parts of its tour (kRowFree: row unused)
+    unsigned int *tmaxn;           // per tour-sum row: deepest length over the parts of its tour
     int *hungry;                   // walks waiting for work
     int *status;
     // optional sampled trace

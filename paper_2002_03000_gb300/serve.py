@@ -150,9 +150,9 @@ class GpuEngine:
         self.bytes_est = {}
 
     def bytes_needed(self, req):
-        # tables + per-walk tour sums and stack spill areas (an upper estimate)
+        # tables + per-walk tour sums (two rows per walk) and stack spill areas (an upper estimate)
         L = req.n_max + 1
-        return 3 * 8 * L + req.n_seq * (8 * L + 12 * req.n_max) + (1 << 20)
+        return 3 * 8 * L + req.n_seq * (16 * L + 12 * req.n_max) + (1 << 20)
 
     def start(self, req):
         torch = self.torch
