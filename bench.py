@@ -540,6 +540,58 @@ def time_to_target(run, cap_s):
     return out
 
 
+LOG_C10000_PAPER = 9704.14   # Sec. 4, eq. 8: log c_10000 on the square lattice (1.6e9 iterations)
+
+
+def long_walks(cap_s=60.0):
+    """Sec. 4's long walks with Table 2's setup: square lattice, n_max = 10^4, 12
+    interacting sequences (Algorithm 2, snapshot thresholds, walks in the global
+    arena), from empty tables, one tour of every sequence per launch until
+    `cap_s` seconds (each launch bounded by that too).  Reports what is reached:
+    tours finished, growth steps, the longest length sampled, and log c_10000 with
+    its standard error against the paper's 9704.14 once n = 10^4 is sampled."""
+    import numpy as np
+    import paper_2002_03000_gb300 as pg
+    n_max, N = 10000, 12
+    out = {"workload": "square lattice, n_max 10^4, 12 interacting sequences, from empty tables; "
+                       "launches of 1, 2, 4, ... up to 16 tours per sequence", "cap_s": cap_s,
+           "log_c10000_paper": LOG_C10000_PAPER, "launches": []}
+    run = pg.Run(2, n_max, N, 1, max_seconds=cap_s)
+    t0 = time.perf_counter()
+    status, chunk = 0, 1
+    while time.perf_counter() - t0 < cap_s:
+        t1 = time.perf_counter()
+        try:
+            run.run(chunk)
+        except pg.PermError as e:
+            status = e.code
+        chunk = min(2 * chunk, 16)
+        st = run.stats()
+        S = run.tables()["S"]
+        reached = int(np.max(np.nonzero(S)[0])) if np.any(S > 0) else 0
+        if len(out["launches"]) < 12:
+            out["launches"].append({"seconds": time.perf_counter() - t1, "tours_finished": st["tours_finished"],
+                                    "steps": st["steps"], "longest_length": reached, "status": st["status"]})
+        if status != 0 or st["status"] != 0:
+            break
+    lc, S, rv = run.estimates()
+    st = run.stats()
+    run.close()
+    wm = {1: "shared memory (one walk per CTA beside the 80 KB snapshot table)", 2: "global arena"}
+    reached = int(np.max(np.nonzero(S)[0])) if np.any(S > 0) else 0
+    out.update({"seconds": time.perf_counter() - t0, "tours_finished": st["tours_finished"],
+                "steps": st["steps"], "longest_length": reached,
+                "stopped_by": "time bound of a launch (PERM_ETIMEOUT)" if status or st["status"] else
+                              ("cap" if reached < n_max else "n_max reached"),
+                "walk_memory": wm.get(st["walk_memory"], str(st["walk_memory"]))})
+    if reached >= n_max and math.isfinite(lc[n_max]):
+        out["log_c10000"] = float(lc[n_max])
+        out["log_c10000_se"] = float(math.sqrt(rv[n_max])) if math.isfinite(rv[n_max]) else None
+    else:
+        out["log_c_longest"] = float(lc[reached]) if reached > 0 else None
+    return out
+
+
 def run_ours(args):
     import torch
     world, rank, local = dist_env()
@@ -686,6 +738,7 @@ def run_ours(args):
         line["growth_constant"] = growth_constants((lc, rv))
         line["alg1_vs_alg2"] = alg1_vs_alg2()
         line["perm_cutoffs"] = perm_cutoffs_vs_flatperm()
+        line["long_walks"] = long_walks(args.long_cap_s)
         line["autotune"] = autotuned_run(w["tours"])
         line["batched"] = batched_vs_plain(args.batch_tours)
         line["batched"]["stand_in"] = ("stated config: each of the 96 runs to rel. SE of c_nmax <= 1e-3; "
@@ -716,6 +769,7 @@ def main():
     ap.add_argument("--target-cap-s", type=float, default=60.0)
     ap.add_argument("--skip-systems", action="store_true")
     ap.add_argument("--batch-tours", type=int, default=16)
+    ap.add_argument("--long-cap-s", type=float, default=40.0)
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)

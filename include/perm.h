@@ -93,6 +93,13 @@ typedef struct {
     int observables;   /* 1: also accumulate sum W |omega_n|^2 per length (the squared
                           end-to-end distance, for the ratio estimator of Sec. 1,
                           eq. 5; read with perm_observable_r2); 0 = off (default) */
+    int walk_memory;   /* where each walk's occupancy hash, site list and stack ring
+                          live: 0 = shared memory when at least one walk per CTA fits
+                          beside the snapshot table, else a global-memory arena (long
+                          walks: n_max of 10^4 and more); 1 = shared memory only
+                          (PERM_EUNSUPPORTED when nothing fits); 2 = the global
+                          arena (served through L1 and L2; the snapshot table stays
+                          in shared memory while it fits) */
 } perm_config;
 
 /* Fill cfg with defaults for (d, n_max, n_seq, seed). */
@@ -208,6 +215,9 @@ typedef struct {
     int64_t exact_steps;  /* nodes whose decision evaluated r in double precision because
                              the single-precision estimate lay too close to a decision
                              boundary to settle it, cumulative */
+    int walk_memory;      /* where the walks' hashes, site lists and stack rings live:
+                             1 shared memory, 2 the global arena */
+    int pad;
 } perm_stats_t;
 int perm_stats(perm_handle h, perm_stats_t *out);
 
@@ -333,8 +343,9 @@ int perm_autotune(perm_config *cfg, int64_t probe_tours);
  * whose scratch exceeds the buffer is rejected with PERM_ESCRATCH.  The run
  * grows every waiting copy on the walk that made it (no shared copies:
  * share_copies 0 or -1 both mean that here) and uses the automatic layout;
- * observables, hash_scale, lanes_per_warp, stack_ring, max_ctas other than 0,
- * or share_copies > 0, return PERM_EUNSUPPORTED.  Starts from empty tables and
+ * observables, hash_scale, lanes_per_warp, stack_ring, max_ctas, walk_memory
+ * other than 0, or share_copies > 0, return PERM_EUNSUPPORTED (every walk's
+ * state must then fit in shared memory).  Starts from empty tables and
  * grows tours_per_seq tours of each of cfg->n_seq sequences (M = n_seq *
  * tours_per_seq).
  * W_n, S_n, Q_n: caller-owned DEVICE arrays of n_max+1 entries, overwritten

@@ -47,7 +47,7 @@ class perm_config(C.Structure):
                 ("slots", C.c_int), ("lanes_per_warp", C.c_int), ("refresh_ns", C.c_int),
                 ("max_seconds", C.c_double), ("ramp_c0", C.c_int), ("ramp_gamma", C.c_double),
                 ("max_ctas", C.c_int), ("hash_scale", C.c_int), ("share_copies", C.c_int),
-                ("stack_ring", C.c_int), ("observables", C.c_int)]
+                ("stack_ring", C.c_int), ("observables", C.c_int), ("walk_memory", C.c_int)]
 
 
 class perm_stats_t(C.Structure):
@@ -56,7 +56,8 @@ class perm_stats_t(C.Structure):
                 ("slots", C.c_int), ("ctas", C.c_int), ("lanes_per_warp", C.c_int),
                 ("warps_per_cta", C.c_int), ("hash_slots", C.c_int), ("status", C.c_int),
                 ("device_bytes", C.c_int64), ("tours_finished", C.c_int64),
-                ("shared", C.c_int64), ("exact_steps", C.c_int64)]
+                ("shared", C.c_int64), ("exact_steps", C.c_int64), ("walk_memory", C.c_int),
+                ("pad", C.c_int)]
 
 
 class perm_trace_record(C.Structure):

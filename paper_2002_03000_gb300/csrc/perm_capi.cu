@@ -28,6 +28,9 @@ struct perm_run_s {
     int thresh = perm::kSnapshot;
     int log2h = 0, slots = 0, ctas = 0, worker_warps = 0, lanes = 0, stride = 32, stack_cache = 16;
     size_t smem = 0;
+    int arena_mode = 0;            // perm::ArenaMode
+    long long arena_cta_bytes = 0;
+    unsigned char *arena = nullptr;
     int ntab = 1;
     int xrows = 0;                 // tour-sum rows: one per walk, two with shared copies
     // device buffers
@@ -83,7 +86,7 @@ void free_all(perm_handle h) {
                     h->max_stack, h->copies, h->refreshes, h->iterations, h->finished, h->exact_steps,
                     h->trace_count, h->gstk_meta, h->status, h->trace,
                     h->trace_coords, h->dq_cells, h->dq_head, h->dq_tail, h->dq_ready, h->dq_free, h->outst,
-                    h->tmaxn, h->hungry, h->cut};
+                    h->tmaxn, h->hungry, h->cut, h->arena};
     for (void *p : ptrs) if (p) cudaFree(p);
 }
 
@@ -125,6 +128,7 @@ void perm_config_init(perm_config *cfg, int d, int n_max, int n_seq, uint64_t se
     cfg->share_copies = 0;
     cfg->stack_ring = 0;
     cfg->observables = 0;
+    cfg->walk_memory = 0;
 }
 
 const char *perm_strerror(int code) {
@@ -164,6 +168,7 @@ int create_impl(perm_handle *out, const perm_config *cfg, const ForcedLayout *fo
     if (cfg->max_ctas < -1 || cfg->hash_scale < 0 || cfg->hash_scale > 2) return PERM_EINVAL;
     if (cfg->share_copies < -1 || cfg->share_copies > 1024) return PERM_EINVAL;
     if (cfg->observables != 0 && cfg->observables != 1) return PERM_EINVAL;
+    if (cfg->walk_memory < 0 || cfg->walk_memory > 2) return PERM_EINVAL;
     if (cfg->stack_ring != 0 && cfg->stack_ring != 16 && cfg->stack_ring != 32 &&
         cfg->stack_ring != 64 && cfg->stack_ring != 128) return PERM_EINVAL;
     const int lpw = cfg->lanes_per_warp;
@@ -209,7 +214,20 @@ int create_impl(perm_handle *out, const perm_config *cfg, const ForcedLayout *fo
     const bool snap = (h->thresh == perm::kSnapshot);
     const size_t budget = force ? force->smem_budget : prop.sharedMemPerBlockOptin;
     auto pow2_at_least = [](int v) { int p = 1; while (p < v) p <<= 1; return p; };
+    // where the walks' hashes, site lists and stack rings live: shared memory, or a
+    // global arena when asked for or when not one walk per CTA fits beside the head
+    const size_t head_b = perm::cta_head_bytes(n_max, snap);
+    auto arena_for = [&](int wm) {
+        if (wm != 2) return (int)perm::kArenaNone;
+        return head_b <= budget ? (int)perm::kArenaWalks : (int)perm::kArenaAll;
+    };
+    int arena_mode = arena_for(force ? 1 : cfg->walk_memory);
+    if (!force && cfg->walk_memory == 0 &&
+        perm::cta_smem_bytes(d, key64, n_max, log2h, h->stack_cache, 1, snap, 1) > budget)
+        arena_mode = arena_for(2);
     auto smem_for = [&](int warps, int stride) {
+        if (arena_mode == perm::kArenaWalks) return head_b;
+        if (arena_mode == perm::kArenaAll) return (size_t)0;
         return perm::cta_smem_bytes(d, key64, n_max, log2h, h->stack_cache, warps, snap, stride);
     };
     if (!force && cfg->max_ctas == -1) {
@@ -279,6 +297,14 @@ int create_impl(perm_handle *out, const perm_config *cfg, const ForcedLayout *fo
     h->stride = stride;
     h->slots = (int)slots;
     h->smem = smem_for(warps, stride);
+    h->arena_mode = arena_mode;
+    if (arena_mode != perm::kArenaNone) {
+        const size_t wb = perm::cta_warp_bytes(key64, n_max, log2h, h->stack_cache, stride);
+        h->arena_cta_bytes = (long long)(wb * (size_t)warps + (arena_mode == perm::kArenaAll ? head_b : 0));
+        h->arena_cta_bytes = (h->arena_cta_bytes + 255) & ~255LL;
+        // at most 64 GB of walk state
+        if ((double)h->arena_cta_bytes * h->ctas > 64e9) { cudaStreamDestroy(h->stream); delete h; return PERM_ENOMEM; }
+    }
 
     const size_t L = (size_t)n_max + 1;
     h->ntab = (cfg->alg == PERM_ALG1) ? n_seq : 1;
@@ -294,6 +320,8 @@ int create_impl(perm_handle *out, const perm_config *cfg, const ForcedLayout *fo
     if (rc == PERM_OK) rc = dalloc(h, &h->X, L * (size_t)h->xrows);
     if (rc == PERM_OK) rc = dalloc(h, &h->gstk_meta, (size_t)n_max * h->slots);
     if (rc == PERM_OK) rc = dalloc(h, &h->gstk_w, (size_t)n_max * h->slots);
+    if (rc == PERM_OK && h->arena_mode != perm::kArenaNone)
+        rc = dalloc(h, &h->arena, (size_t)h->arena_cta_bytes * (size_t)h->ctas);
     if (rc == PERM_OK) rc = dalloc(h, &h->steps, 1);
     if (rc == PERM_OK) rc = dalloc(h, &h->max_stack, 1);
     if (rc == PERM_OK) rc = dalloc(h, &h->copies, 1);
@@ -361,6 +389,7 @@ static RunDev make_params(perm_handle h) {
     P.log2h = h->log2h; P.S = h->lanes; P.stride = h->stride;
     P.worker_warps = h->worker_warps; P.slots = h->slots;
     P.stack_cache = h->stack_cache;
+    P.arena_mode = h->arena_mode; P.arena = h->arena; P.arena_cta_bytes = h->arena_cta_bytes;
     P.key0 = (uint32_t)h->cfg.seed ^ h->cfg.run_id;
     P.key1 = (uint32_t)(h->cfg.seed >> 32);
     P.tour_limit = h->tour_limit;
@@ -653,6 +682,8 @@ int perm_stats(perm_handle h, perm_stats_t *out) {
     out->tours_finished = (int64_t)fin;
     out->shared = (int64_t)shr;
     out->exact_steps = (int64_t)ex;
+    out->walk_memory = h->arena_mode == perm::kArenaNone ? 1 : 2;
+    out->pad = 0;
     return PERM_OK;
 }
 
@@ -764,7 +795,7 @@ int member_reset(perm_handle h) {
 namespace {
 
 constexpr char kCkptMagic[8] = {'P', 'E', 'R', 'M', 'C', 'K', 'P', '1'};
-constexpr uint32_t kCkptVersion = 2;
+constexpr uint32_t kCkptVersion = 3;
 
 struct CkptHeader {
     char magic[8];

@@ -248,20 +248,35 @@ __device__ __forceinline__ void grow_run(const RunDev &P, unsigned char *smem, c
     const bool snapshot = (MODE == kSnapshot);
     const int K = P.stack_cache;
 
-    CtaHead *head = reinterpret_cast<CtaHead *>(smem);
-    double *aoc = reinterpret_cast<double *>(smem + 64);
-    unsigned char *p = smem + 64 + 1024;
+    // The CTA's state: the head region (header, constant tables, snapshot of W_n)
+    // and one region per walk warp (occupancy hashes, site lists, stack rings).
+    // Both sit in shared memory, or, for walks too long for it, the walk regions
+    // (and, if even the head does not fit, the head too) in this CTA's slice of a
+    // global arena, served through L1 and L2.  Each walk's data is touched by its
+    // own thread only, so the same code runs on either.
+    const int ST = P.stride;
+    const size_t hbytes = head_region_bytes(P.n_max, snapshot);
+    const size_t wbytes = warp_region_bytes(P.n_max, P.log2h, K, sizeof(Key), ST);
+    unsigned char *hbase = smem, *wbase = smem + hbytes;
+    if (P.arena_mode != kArenaNone) {
+        unsigned char *a = P.arena + (size_t)blockIdx.x * (size_t)P.arena_cta_bytes;
+        if (P.arena_mode == kArenaAll) { hbase = a; wbase = a + hbytes; }
+        else wbase = a;
+    }
+    CtaHead *head = reinterpret_cast<CtaHead *>(hbase);
+    double *aoc = reinterpret_cast<double *>(hbase + 64);
+    unsigned char *p = hbase + 64 + 1024;
     double *Wsnap = nullptr;
     if (snapshot) {
         Wsnap = reinterpret_cast<double *>(p); p += 8 * (size_t)L;
     }
-    const int ST = P.stride;
-    const size_t wbytes = warp_region_bytes(P.n_max, P.log2h, K, sizeof(Key), ST);
-    const size_t total = head_region_bytes(P.n_max, snapshot) + wbytes * P.worker_warps;
 
-    // zero everything (empty hashes, zero deltas), then the constant tables
-    for (size_t i = threadIdx.x; i < total / 16; i += blockDim.x)
-        reinterpret_cast<uint4 *>(smem)[i] = make_uint4(0u, 0u, 0u, 0u);
+    // zero everything (empty hashes, empty stacks), then the constant tables
+    for (size_t i = threadIdx.x; i < hbytes / 16; i += blockDim.x)
+        reinterpret_cast<uint4 *>(hbase)[i] = make_uint4(0u, 0u, 0u, 0u);
+    for (size_t i = threadIdx.x; i < wbytes * P.worker_warps / 16; i += blockDim.x)
+        reinterpret_cast<uint4 *>(wbase)[i] = make_uint4(0u, 0u, 0u, 0u);
+    if (P.arena_mode != kArenaNone) __threadfence_block();
     __syncthreads();
     fill_aoc(aoc, D, threadIdx.x, blockDim.x);
     const long long limit = P.tour_limit;
@@ -337,7 +352,7 @@ __device__ __forceinline__ void grow_run(const RunDev &P, unsigned char *smem, c
     // ----------------------------------------------------------------------
     // worker warps
     // ----------------------------------------------------------------------
-    unsigned char *wb = smem + head_region_bytes(P.n_max, snapshot) + wbytes * warp;
+    unsigned char *wb = wbase + wbytes * warp;
     Key *hash = reinterpret_cast<Key *>(wb);
     uint16_t *sites = reinterpret_cast<uint16_t *>(
         wb + (((((size_t)1 << P.log2h) * ST * sizeof(Key)) + 15) & ~(size_t)15));
@@ -1157,6 +1172,12 @@ size_t cta_smem_bytes(int d, bool key64, int n_max, int log2h, int stack_cache, 
            warp_region_bytes(n_max, log2h, stack_cache, key64 ? 8 : 4, stride) * (size_t)worker_warps;
 }
 
+size_t cta_head_bytes(int n_max, bool snapshot) { return head_region_bytes(n_max, snapshot); }
+
+size_t cta_warp_bytes(bool key64, int n_max, int log2h, int stack_cache, int stride) {
+    return warp_region_bytes(n_max, log2h, stack_cache, key64 ? 8 : 4, stride);
+}
+
 namespace {
 template <int D, typename Key, int MODE>
 cudaError_t allow_smem() {
@@ -1175,8 +1196,12 @@ cudaError_t allow_smem() {
 template <int D, typename Key, int MODE>
 cudaError_t launch_one(const RunDev &P, int ctas, cudaStream_t stream) {
     const bool snapshot = (MODE == kSnapshot);
-    const size_t smem = cta_smem_bytes(D, sizeof(Key) == 8, P.n_max, P.log2h, P.stack_cache,
-                                       P.worker_warps, snapshot, P.stride);
+    // shared memory holds what the arena does not
+    const size_t smem = P.arena_mode == kArenaAll ? 0
+                      : (P.arena_mode == kArenaWalks ? head_region_bytes(P.n_max, snapshot)
+                                                     : cta_smem_bytes(D, sizeof(Key) == 8, P.n_max, P.log2h,
+                                                                      P.stack_cache, P.worker_warps, snapshot,
+                                                                      P.stride));
     cudaError_t e = allow_smem<D, Key, MODE>();
     if (e != cudaSuccess) return e;
     const int threads = 32 * (P.worker_warps + (snapshot ? 1 : 0));

@@ -9,6 +9,9 @@
 namespace perm {
 
 enum ThreshMode { kSnapshot = 0, kFresh = 1 };
+// Where a CTA's state lives: all in shared memory; the walk regions in a global
+// arena (head in shared memory); or all of it in the arena.
+enum ArenaMode { kArenaNone = 0, kArenaWalks = 1, kArenaAll = 2 };
 
 // Everything one persistent launch needs (passed by value).
 struct RunDev {
@@ -20,6 +23,9 @@ struct RunDev {
     int worker_warps;    // per CTA
     int slots;           // walks on the device
     int stack_cache;     // stack records cached per walk in shared memory (power of 2)
+    int arena_mode;      // ArenaMode
+    long long arena_cta_bytes;     // bytes of one CTA's slice of the arena
+    unsigned char *arena;          // global arena (nullptr unless arena_mode != kArenaNone)
     uint32_t key0, key1; // Philox key
     long long tour_limit;      // Alg. 2: tickets below this are tours of this launch or earlier
     long long seq_target;      // Alg. 1: tours per sequence after this launch
@@ -107,9 +113,11 @@ int member_params(perm_handle h, int64_t tours_per_seq, int run_index, RunDev *P
 // Empty tables and tour sums (every row, also after a failed run), on the run's stream.
 int member_reset(perm_handle h);
 
-// Shared-memory bytes of one CTA.
+// Shared-memory bytes of one CTA (everything in shared memory), and its parts.
 size_t cta_smem_bytes(int d, bool key64, int n_max, int log2h, int stack_cache, int worker_warps,
                       bool snapshot, int stride);
+size_t cta_head_bytes(int n_max, bool snapshot);
+size_t cta_warp_bytes(bool key64, int n_max, int log2h, int stack_cache, int stride);
 
 cudaError_t launch_grow(const RunDev &P, int thresh_mode, bool key64, int ctas,
                         cudaStream_t stream);

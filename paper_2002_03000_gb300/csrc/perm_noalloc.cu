@@ -64,10 +64,11 @@ extern "C" int perm_run_static(const perm_config *cfg, int64_t tours_per_seq, do
     if (cfg->slots < 0 || cfg->refresh_ns < 0 || !(cfg->max_seconds >= 0.0)) return PERM_EINVAL;
     if (!(cfg->ramp_gamma >= 0.0) || cfg->ramp_gamma > 1e6) return PERM_EINVAL;
     // settings this entry point does not carry out are refused, not ignored: the
-    // eq. 5 sums, a chosen layout (walks per warp, hash size, stack ring, CTA cap)
-    // and shared copies (the run grows every copy on the walk that made it)
+    // eq. 5 sums, a chosen layout (walks per warp, hash size, stack ring, CTA cap,
+    // walk memory) and shared copies (the run grows every copy on the walk that
+    // made it)
     if (cfg->observables != 0 || cfg->hash_scale != 0 || cfg->lanes_per_warp != 0 ||
-        cfg->stack_ring != 0 || cfg->max_ctas != 0 || cfg->share_copies > 0)
+        cfg->stack_ring != 0 || cfg->max_ctas != 0 || cfg->share_copies > 0 || cfg->walk_memory != 0)
         return PERM_EUNSUPPORTED;
     const bool key64 = (d == 3 && n_max > 512);
     if (n_max > (d == 2 ? 32766 : (key64 ? (1 << 20) - 2 : 512))) return PERM_EUNSUPPORTED;
