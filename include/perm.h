@@ -308,6 +308,12 @@ int perm_batch_create(perm_batch_handle *out, const perm_config *cfgs, const int
 int perm_batch_create_persistent(perm_batch_handle *out, const perm_config *cfgs,
                                  const int64_t *tours_per_seq, int R);
 int perm_batch_run(perm_batch_handle b);
+/* Grow extra_tours_per_seq[r] more tours per sequence of every run r on top of
+ * its current tables (cumulative, as perm_run; 0 leaves a run as it is, e.g. one
+ * that has met its target error), in one launch of the batch's form (the
+ * persistent kernel over the runs with tours to grow, or each run's kernel on
+ * its stream), and wait.  extra_tours_per_seq: host array of R values >= 0. */
+int perm_batch_continue(perm_batch_handle b, const int64_t *extra_tours_per_seq);
 int perm_batch_size(perm_batch_handle b);
 int perm_batch_estimates(perm_batch_handle b, int r, double *log_cn, double *S_n, double *relvar_n);
 int perm_batch_stats(perm_batch_handle b, int r, perm_stats_t *out);
@@ -316,11 +322,15 @@ void perm_batch_destroy(perm_batch_handle b);
 /* Autotuner (no counterpart in the paper): for each walks-per-warp choice (auto,
  * 2, 4, 8, 16, 32), hash size (hash_scale 0, 1) and stack ring (16, 64 records),
  * times a complete run of probe_tours tours per sequence of cfg from empty
- * tables (twice; the faster counts), and writes the fastest choice into
- * cfg->lanes_per_warp, cfg->hash_scale and cfg->stack_ring.  Equal tours in
- * every trial, so the comparison is at equal work, start-up included.  Results are cached per (d, n_max, n_seq,
- * max_ctas, alg, threshold) for the process.  Synchronous; allocates and frees
- * a handle per trial.  Returns PERM_EUNSUPPORTED if no trial ran. */
+ * tables (twice; the faster counts).  The default layout (auto, 0, 16) is timed
+ * first and kept unless another choice is at least 3% faster and then faster
+ * again on runs of 4 x probe_tours, so the pick is never slower than the
+ * default on that validation.  Writes the choice into cfg->lanes_per_warp,
+ * cfg->hash_scale and cfg->stack_ring.  Equal tours in every trial, so the
+ * comparison is at equal work, start-up included.  Results are cached per (d,
+ * n_max, n_seq, max_ctas, alg, threshold) for the process.  Synchronous;
+ * allocates and frees a handle per trial.  Returns PERM_EUNSUPPORTED if no
+ * trial ran. */
 int perm_autotune(perm_config *cfg, int64_t probe_tours);
 
 /* perm_run_static -- one complete Algorithm-2 growth run that allocates

@@ -35,7 +35,7 @@ EXPORTS = (
     "perm_trace_read", "perm_destroy", "perm_strerror", "perm_debug_step", "perm_debug_philox",
     "perm_run_static", "perm_set_cutoffs", "perm_save", "perm_load", "perm_get_config", "perm_batch_create", "perm_batch_create_persistent", "perm_batch_run", "perm_batch_size",
     "perm_batch_estimates", "perm_batch_stats", "perm_batch_destroy", "perm_autotune",
-    "perm_observable_r2", "perm_estimates_from_tables",
+    "perm_observable_r2", "perm_estimates_from_tables", "perm_batch_continue",
 )
 PERM_COMBINE_MEAN = 0
 PERM_COMBINE_GEOMETRIC = 1
@@ -120,6 +120,7 @@ def load(path: str = LIB_PATH):
     L.perm_get_config.argtypes = [vp, C.POINTER(perm_config)]
     L.perm_batch_create_persistent.argtypes = [hp, C.POINTER(perm_config), C.POINTER(i64), C.c_int]
     L.perm_batch_run.argtypes = [vp]
+    L.perm_batch_continue.argtypes = [vp, C.POINTER(i64)]
     L.perm_batch_size.argtypes = [vp]
     L.perm_batch_estimates.argtypes = [vp, C.c_int, dp, dp, dp]
     L.perm_batch_stats.argtypes = [vp, C.c_int, C.POINTER(perm_stats_t)]
@@ -324,6 +325,11 @@ def perm_batch_create_persistent(cfgs, tours):
 
 def perm_batch_run(b):
     _check(load().perm_batch_run(b), "perm_batch_run")
+
+
+def perm_batch_continue(b, extra_tours):
+    arr = (C.c_int64 * len(extra_tours))(*[int(t) for t in extra_tours])
+    _check(load().perm_batch_continue(b, arr), "perm_batch_continue")
 
 
 def perm_batch_estimates(b, r, n_max):

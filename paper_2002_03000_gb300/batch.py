@@ -32,6 +32,28 @@ class Batch:
     def run(self):
         nat.perm_batch_run(self.b)
 
+    def continue_runs(self, extra_tours):
+        """More tours per sequence for each run on top of its tables (0: leave it)."""
+        nat.perm_batch_continue(self.b, extra_tours)
+
+    def run_to_target(self, target, first_tours=None, max_rounds=8, max_tours=1 << 16):
+        """Every run until the relative standard error of its c_{n_max} is at most
+        `target`: a replay from empty tables (the creation-time tours), then
+        continuations that give each run still above its target the tours the
+        1/tours law of the variance predicts it needs (at least 4 more, at most
+        8 times what it has), until all meet it or `max_rounds`.  Returns the
+        tours per sequence each run grew and the rounds taken."""
+        self.run()
+        tours = list(self.tours)
+        for rnd in range(max_rounds):
+            extra = [more_tours(self.estimates(r)[2][cfg.n_max], tours[r], target, max_tours)
+                     for r, cfg in enumerate(self.run_cfgs)]
+            if not any(extra):
+                return tours, rnd
+            self.continue_runs(extra)
+            tours = [t + e for t, e in zip(tours, extra)]
+        return tours, max_rounds
+
     def estimates(self, r):
         return nat.perm_batch_estimates(self.b, r, self.run_cfgs[r].n_max)
 
@@ -54,6 +76,18 @@ class Batch:
             self.close()
         except Exception:
             pass
+
+
+def more_tours(relvar, tours, target, max_tours=1 << 16):
+    """Tours per sequence to add to a run with `tours` whose c_{n_max} has relative
+    variance `relvar`, to bring its relative standard error to `target`: 0 when
+    met; else what the 1/tours law of the variance predicts (10% over), at least
+    4 and at most 8 times what it has."""
+    rel = math.sqrt(relvar) if relvar >= 0 and math.isfinite(relvar) else float("inf")
+    if rel <= target or tours >= max_tours:
+        return 0
+    want = tours * ((rel / target) ** 2 - 1.0) if math.isfinite(rel) else tours
+    return int(min(max(math.ceil(1.1 * want), 4), 8 * tours, max_tours - tours))
 
 
 def make_config(d, n_max, n_seq, seed, run_id=0, **kw):

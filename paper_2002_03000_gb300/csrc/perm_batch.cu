@@ -40,6 +40,11 @@ struct perm_batch_s {
     // persistent form
     perm::RunDev *d_runs = nullptr;
     int *d_ctl = nullptr;
+    bool persistent = false;
+    int grid = 0, threads = 0;
+    size_t smem = 0;
+    long long max_ns = 0;
+    std::vector<perm::RunDev> P0;   // the descriptors a replay grows (from empty tables)
 };
 
 namespace {
@@ -175,6 +180,11 @@ int perm_batch_create_persistent(perm_batch_handle *out, const perm_config *cfgs
         max_s = std::max(max_s, (double)P[r].max_ns * 1e-9);
     }
     const int threads = 32 * (warps + 1);
+    b->persistent = true;
+    b->grid = grid;
+    b->threads = threads;
+    b->smem = smem;
+    b->max_ns = (long long)(max_s * 1e9);
     // every CTA of the grid must be resident at once: walks wait (boundedly) on
     // copies that other CTAs' walks hand over
     int resident = 0;
@@ -209,6 +219,7 @@ int perm_batch_create_persistent(perm_batch_handle *out, const perm_config *cfgs
     }
     // the resets above cleared the host-side tour counts; set them again
     for (int r = 0; rc == PERM_OK && r < R; ++r) rc = perm::member_params(b->runs[r], b->tours[r], r, &P[r], nullptr, nullptr);
+    if (rc == PERM_OK) b->P0 = P;
     if (rc != PERM_OK) {
         batch_free(b);
         return rc;
@@ -219,8 +230,64 @@ int perm_batch_create_persistent(perm_batch_handle *out, const perm_config *cfgs
 
 int perm_batch_run(perm_batch_handle b) {
     if (!b || !b->exec) return PERM_EINVAL;
+    // a replay grows every run from empty tables by its creation-time tours, also
+    // after perm_batch_continue moved the descriptors and tour counts on
+    if (b->persistent && cudaMemcpyAsync(b->d_runs, b->P0.data(), sizeof(perm::RunDev) * b->R,
+                                         cudaMemcpyHostToDevice, b->origin) != cudaSuccess)
+        return PERM_EDEVICE;
     if (cudaGraphLaunch(b->exec, b->origin) != cudaSuccess) return PERM_EDEVICE;
     if (cudaStreamSynchronize(b->origin) != cudaSuccess) return PERM_EDEVICE;
+    for (int r = 0; r < b->R; ++r) {
+        perm::RunDev P;
+        const int rc = perm::member_params(b->runs[r], b->tours[r], r, &P, nullptr, nullptr);
+        if (rc != PERM_OK) return rc;
+    }
+    for (perm_handle h : b->runs) {
+        perm_stats_t st;
+        const int rc = perm_stats(h, &st);
+        if (rc != PERM_OK) return rc;
+        if (st.status != PERM_OK) return st.status;
+    }
+    return PERM_OK;
+}
+
+int perm_batch_continue(perm_batch_handle b, const int64_t *extra_tours_per_seq) {
+    if (!b || !extra_tours_per_seq) return PERM_EINVAL;
+    for (int r = 0; r < b->R; ++r)
+        if (extra_tours_per_seq[r] < 0) return PERM_EINVAL;
+    if (!b->persistent) {
+        // each run's own kernel on its stream, cumulative on its tables
+        for (int r = 0; r < b->R; ++r) {
+            if (extra_tours_per_seq[r] == 0) continue;
+            const int rc = perm_run(b->runs[r], extra_tours_per_seq[r]);
+            if (rc != PERM_OK) return rc;
+        }
+        for (cudaStream_t s : b->streams)
+            if (cudaStreamSynchronize(s) != cudaSuccess) return PERM_EDEVICE;
+    } else {
+        // one persistent launch over the runs with tours to grow; the others keep
+        // their tables (every CTA skips a run with no tours left to start)
+        std::vector<perm::RunDev> P(b->R);
+        for (int r = 0; r < b->R; ++r) {
+            const int rc = perm::member_extend(b->runs[r], extra_tours_per_seq[r], r, &P[r]);
+            if (rc != PERM_OK) return rc;
+        }
+        if (cudaMemcpyAsync(b->d_runs, P.data(), sizeof(perm::RunDev) * b->R, cudaMemcpyHostToDevice,
+                            b->origin) != cudaSuccess)
+            return PERM_EDEVICE;
+        perm::BatchDev B;
+        B.runs = b->d_runs;
+        B.R = b->R;
+        B.active = b->d_ctl;
+        B.granted = b->d_ctl + b->R;
+        B.closed = b->d_ctl + 2 * b->R;
+        B.runs_open = b->d_ctl + 3 * b->R;
+        B.max_ns = b->max_ns;
+        if (perm::launch_batch(B, b->grid, b->threads, b->smem, b->origin) != cudaSuccess) return PERM_EDEVICE;
+        for (int r = 0; r < b->R; ++r)
+            if (perm::launch_finalize(P[r].tickets, P[r].tour_limit, b->origin) != cudaSuccess) return PERM_EDEVICE;
+        if (cudaStreamSynchronize(b->origin) != cudaSuccess) return PERM_EDEVICE;
+    }
     for (perm_handle h : b->runs) {
         perm_stats_t st;
         const int rc = perm_stats(h, &st);
@@ -248,8 +315,10 @@ void perm_batch_destroy(perm_batch_handle b) { batch_free(b); }
 // Autotuner: short calibration runs over walks per warp, hash size and the
 // shared-memory stack ring ("spill tile").  Each trial times a complete run of
 // probe_tours tours per sequence from empty tables (twice, the faster counts),
-// so the trials compare equal work, start-up included.  The best
-// choice is written back and cached per (d, n_max, n_seq, max_ctas, alg, threshold).
+// so the trials compare equal work, start-up included.  The default layout is
+// timed first and stays unless a choice beats it by 3% and then again on runs
+// of four times the tours.  The choice is written back and cached per (d,
+// n_max, n_seq, max_ctas, alg, threshold).
 // ---------------------------------------------------------------------------
 namespace {
 struct TuneChoice { int lanes, hash_scale, ring; };
@@ -273,36 +342,53 @@ int perm_autotune(perm_config *cfg, int64_t probe_tours) {
     const int lanes_c[] = {0, 2, 4, 8, 16, 32};
     const int hash_c[] = {0, 1};
     const int ring_c[] = {16, 64};
-    double best_s = -1.0;
-    TuneChoice best{0, 0, 0};
+    // a complete run of `tours` from empty tables with the layout of `t`, twice
+    // (start-up included: it is part of every run); the faster of the two counts
+    auto time_layout = [&](const TuneChoice &t, int64_t tours) {
+        perm_config c = *cfg;
+        c.lanes_per_warp = t.lanes;
+        c.hash_scale = t.hash_scale;
+        c.stack_ring = t.ring;
+        perm_handle h = nullptr;
+        if (perm_create_ex(&h, &c) != PERM_OK) return -1.0;
+        double sec = -1.0;
+        int rc = PERM_OK;
+        for (int rep = 0; rep < 2 && rc == PERM_OK; ++rep) {
+            rc = perm_reset(h);
+            const auto t0 = std::chrono::steady_clock::now();
+            if (rc == PERM_OK) rc = perm_run_sync(h, tours);
+            const auto t1 = std::chrono::steady_clock::now();
+            const double s1 = std::chrono::duration<double>(t1 - t0).count();
+            if (rc == PERM_OK && (sec < 0.0 || s1 < sec)) sec = s1;
+        }
+        perm_destroy(h);
+        return rc == PERM_OK ? sec : -1.0;
+    };
+    const TuneChoice dflt{0, 0, 16};
+    const double dflt_s = time_layout(dflt, probe_tours);
+    double best_s = dflt_s;
+    TuneChoice best = dflt;
     for (int ring : ring_c) {
         for (int hs : hash_c) {
             for (int lw : lanes_c) {
-                perm_config c = *cfg;
-                c.lanes_per_warp = lw;
-                c.hash_scale = hs;
-                c.stack_ring = ring;
-                perm_handle h = nullptr;
-                if (perm_create_ex(&h, &c) != PERM_OK) continue;
-                // a complete run of probe_tours from empty tables, twice (start-up
-                // included: it is part of every run); the faster of the two counts
-                double sec = -1.0;
-                int rc = PERM_OK;
-                for (int rep = 0; rep < 2 && rc == PERM_OK; ++rep) {
-                    rc = perm_reset(h);
-                    const auto t0 = std::chrono::steady_clock::now();
-                    if (rc == PERM_OK) rc = perm_run_sync(h, probe_tours);
-                    const auto t1 = std::chrono::steady_clock::now();
-                    const double s1 = std::chrono::duration<double>(t1 - t0).count();
-                    if (rc == PERM_OK && (sec < 0.0 || s1 < sec)) sec = s1;
-                }
-                if (rc == PERM_OK && sec >= 0.0 && (best_s < 0.0 || sec < best_s)) {
+                const TuneChoice t{lw, hs, ring};
+                if (lw == 0 && hs == 0 && ring == 16) continue;
+                const double sec = time_layout(t, probe_tours);
+                // a choice other than the default has to beat it by 3% (the spread
+                // of repeated complete runs), else the default stays
+                if (sec >= 0.0 && (best_s < 0.0 || sec < best_s * (best.lanes == 0 && best.hash_scale == 0 &&
+                                                                     best.ring == 16 ? 0.97 : 1.0))) {
                     best_s = sec;
-                    best = TuneChoice{lw, hs, ring};
+                    best = t;
                 }
-                perm_destroy(h);
             }
         }
+    }
+    // the pick is validated against the default on runs four times as long, and
+    // kept only if it is faster there too
+    if (best_s >= 0.0 && !(best.lanes == 0 && best.hash_scale == 0 && best.ring == 16)) {
+        const double b4 = time_layout(best, 4 * probe_tours), d4 = time_layout(dflt, 4 * probe_tours);
+        if (b4 < 0.0 || (d4 >= 0.0 && b4 >= d4 * 0.98)) { best = dflt; best_s = dflt_s; }
     }
     if (best_s < 0.0) return PERM_EUNSUPPORTED;
     cfg->lanes_per_warp = best.lanes;

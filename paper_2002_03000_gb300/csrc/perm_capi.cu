@@ -775,6 +775,14 @@ int member_params(perm_handle h, int64_t tours_per_seq, int run_index, RunDev *P
     return PERM_OK;
 }
 
+int member_extend(perm_handle h, int64_t extra_tours_per_seq, int run_index, RunDev *P) {
+    if (!h || !P || extra_tours_per_seq < 0) return PERM_EINVAL;
+    h->tour_limit += extra_tours_per_seq * (long long)h->cfg.n_seq;
+    *P = make_params(h);
+    P->run_index = run_index;
+    return PERM_OK;
+}
+
 int member_reset(perm_handle h) {
     int rc = perm_reset(h);
     if (rc != PERM_OK) return rc;

@@ -1090,13 +1090,15 @@ __global__ void __launch_bounds__(32 * 9, 1) batch_kernel(const BatchDev B) {
 }
 
 // Scheduling counters of a batch launch: nothing granted, no CTA on a run; a run
-// with no tours to grow counts as closed.
+// with no tours left to start counts as closed.
 __global__ void batch_init_kernel(const BatchDev B) {
     __shared__ int open;
     if (threadIdx.x == 0) open = 0;
     __syncthreads();
     for (int r = threadIdx.x; r < B.R; r += blockDim.x) {
-        const bool grows = B.runs[r].tour_limit > 0;
+        // a run grows in this launch if it has tours left to start (a continued
+        // batch leaves retired runs with none)
+        const bool grows = B.runs[r].tour_limit > (long long)*(volatile unsigned long long *)B.runs[r].tickets;
         B.active[r] = 0;
         B.granted[r] = 0;
         B.closed[r] = grows ? 0 : 3;

@@ -112,6 +112,9 @@ int member_params(perm_handle h, int64_t tours_per_seq, int run_index, RunDev *P
                   int *worker_warps);
 // Empty tables and tour sums (every row, also after a failed run), on the run's stream.
 int member_reset(perm_handle h);
+// The descriptor after extra_tours_per_seq more tours per sequence on top of the
+// run's current tables (cumulative, as perm_run).
+int member_extend(perm_handle h, int64_t extra_tours_per_seq, int run_index, RunDev *P);
 
 // Shared-memory bytes of one CTA (everything in shared memory), and its parts.
 size_t cta_smem_bytes(int d, bool key64, int n_max, int log2h, int stack_cache, int worker_warps,

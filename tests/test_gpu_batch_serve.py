@@ -139,3 +139,47 @@ def test_served_interacting_requests_meet_exact_counts_and_the_oracle(exact_coun
         lco, rvo = ref[r.d]
         zo = (lc - lco)[2:] / np.sqrt(rv[2:] + rvo[2:] + 1e-10)
         assert np.all(np.abs(zo) < 4.5), (r.rid, zo)
+
+
+def test_batch_continue_equals_runs_alone():
+    """A streams batch of deterministic runs (one sequence, fresh thresholds)
+    replayed and then continued run by run equals each run grown alone by the
+    same total tours; a run given no extra tours keeps its tables; a later replay
+    starts every run again from its creation-time tours."""
+    torch_cuda()
+    spec = [(2, 40, 21, 100, 60), (3, 30, 22, 80, 0), (2, 64, 23, 50, 25)]
+    cfgs = [pb.make_config(d, n, 1, s, threshold=pg.PERM_THRESH_FRESH, max_seconds=120.0)
+            for d, n, s, _, _ in spec]
+    with pb.Batch(cfgs, [t for *_, t, _ in spec]) as b:
+        b.run()
+        before = [b.estimates(r) for r in range(len(spec))]
+        b.continue_runs([e for *_, e in spec])
+        for r, (d, n, s, t, e) in enumerate(spec):
+            (lc0, S0, rv0), _ = _alone(d, n, s, t + e)
+            lc, S, rv = b.estimates(r)
+            assert np.array_equal(S, S0), r
+            fin = np.isfinite(lc0)
+            assert np.allclose(lc[fin], lc0[fin], rtol=0, atol=1e-12), r
+            if e == 0:
+                assert np.array_equal(S, before[r][1])
+        b.run()
+        for r, (d, n, s, t, e) in enumerate(spec):
+            assert np.array_equal(b.estimates(r)[1], before[r][1]), r
+
+
+def test_persistent_batch_runs_to_target(exact_counts):
+    """A persistent batch driven to a common target error: every run meets it,
+    tours grown on top of the first replay add up (S_0 = M exactly), and the
+    estimates stay within 5 standard errors of exact c_n."""
+    torch_cuda()
+    spec = [(2, 16, 300), (3, 11, 400), (2, 16, 600), (3, 11, 200)]
+    cfgs = [pb.make_config(d, n, N, 31 + i, max_seconds=120.0) for i, (d, n, N) in enumerate(spec)]
+    with pb.Batch(cfgs, [8] * len(spec), persistent=True) as b:
+        tours, rounds = b.run_to_target(3e-3)
+        assert 1 <= rounds < 8
+        for r, (d, n, N) in enumerate(spec):
+            lc, S, rv = b.estimates(r)
+            assert math.sqrt(rv[n]) <= 3e-3, r
+            assert S[0] == N * tours[r] and S[1] == N * tours[r]
+            z = zscores(lc, rv, exact_counts[d][: n + 1])
+            assert np.all(np.abs(z[2:]) < 5.0), (r, z)

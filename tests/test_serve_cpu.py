@@ -99,3 +99,17 @@ def test_unmet_requests_retire_at_the_tour_cap():
     req = Request(rid=0, d=2, n_max=64, target=1e-9, arrival=0.0, max_tours=40)
     done = srv.serve([req], idle_sleep=0)
     assert len(done) == 1 and not done[0].met and done[0].tours == 40
+
+
+def test_batch_target_rule():
+    """The tour rule of the to-target drivers: nothing once the target is met,
+    else the 1/tours law of the variance (10% over), at least 4 and at most 8
+    times what the run has; and the Batch wrapper keeps its methods."""
+    from paper_2002_03000_gb300 import batch as pb
+    assert pb.more_tours(0.01 ** 2, 16, 0.02) == 0
+    assert pb.more_tours(0.04 ** 2, 16, 0.03) == 14          # ceil(1.1 x 16 x (16/9 - 1))
+    assert pb.more_tours(0.1 ** 2, 16, 0.01) == 128          # capped at 8 times the tours
+    assert pb.more_tours(0.0301 ** 2, 100, 0.03) == 4        # at least 4
+    assert pb.more_tours(float("inf"), 8, 0.01) == 8
+    for name in ("run", "continue_runs", "run_to_target", "estimates", "stats", "close", "__enter__"):
+        assert hasattr(pb.Batch, name), name
