@@ -110,6 +110,6 @@ def test_batch_target_rule():
     assert pb.more_tours(0.04 ** 2, 16, 0.03) == 14          # ceil(1.1 x 16 x (16/9 - 1))
     assert pb.more_tours(0.1 ** 2, 16, 0.01) == 128          # capped at 8 times the tours
     assert pb.more_tours(0.0301 ** 2, 100, 0.03) == 4        # at least 4
-    assert pb.more_tours(float("inf"), 8, 0.01) == 8
+    assert pb.more_tours(float("inf"), 8, 0.01) == 9           # unknown variance: 1.1 x the tours
     for name in ("run", "continue_runs", "run_to_target", "estimates", "stats", "close", "__enter__"):
         assert hasattr(pb.Batch, name), name
