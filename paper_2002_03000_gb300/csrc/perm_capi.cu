@@ -338,7 +338,9 @@ int create_impl(perm_handle *out, const perm_config *cfg, const ForcedLayout *fo
         int lc = 6;
         while ((1 << lc) < h->slots && lc < 12) ++lc;
         h->dq_log2cap = lc;
-        h->dq_cell_bytes = (int)(32 + ((((size_t)n_max + 1) * (key64 ? 8 : 4) + 15) & ~(size_t)15));
+        // header, the keys of sites 0..n_max, their hash slots (u16)
+        h->dq_cell_bytes = (int)(32 + ((((size_t)n_max + 1) * (key64 ? 8 : 4) + 15) & ~(size_t)15) +
+                                 ((((size_t)n_max + 1) * 2 + 15) & ~(size_t)15));
         const size_t cap = (size_t)1 << lc;
         rc = dalloc(h, &h->dq_cells, cap * (size_t)h->dq_cell_bytes);
         if (rc == PERM_OK) rc = dalloc(h, &h->dq_ready, cap);

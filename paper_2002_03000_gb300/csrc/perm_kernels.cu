@@ -60,13 +60,6 @@ struct CtaHead {
 };
 static_assert(sizeof(CtaHead) == 64, "header size");
 
-// A 16-byte vector of occupancy keys (the walk of a shared copy is moved in these).
-template <typename Key> constexpr int kKeysPerVec = 16 / (int)sizeof(Key);
-template <typename Key> union KeyVec {
-    uint4 v;
-    Key k[16 / sizeof(Key)];
-};
-
 __device__ __forceinline__ long long global_ns() {
     long long t;
     asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
@@ -126,6 +119,28 @@ struct NodeOut {
     bool overflow;
     bool exact;          // the decision was taken on r in double precision
 };
+
+// The whole warp copies a donor's sites 0..bdp (key and hash slot) into a cell.
+template <typename Key>
+__device__ __noinline__ void copy_sites_to_cell(const Key *hash, const uint16_t *sites, int ST, int src,
+                                                int bdp, Key *ck, uint16_t *cs, int lane) {
+    for (int k = lane; k <= bdp; k += 32) {
+        const uint16_t sl = sites[(uint32_t)k * ST + src];
+        ck[k] = hash[(uint32_t)sl * ST + src];
+        cs[k] = sl;
+    }
+}
+
+// The whole warp places a taker's sites 0..dp from a cell at their hash slots.
+template <typename Key>
+__device__ __noinline__ void place_sites_from_cell(Key *hash, uint16_t *sites, int ST, int src, int dp,
+                                                   const Key *ck, const uint16_t *cs, int lane) {
+    for (int k = lane; k <= dp; k += 32) {
+        const uint16_t sl = __ldcg(cs + k);
+        hash[(uint32_t)sl * ST + src] = __ldcg(ck + k);
+        sites[(uint32_t)k * ST + src] = sl;
+    }
+}
 
 // One node's growth step (Sec. 1 and Sec. 2): a_+, r, decision, steps, child
 // weight.  Wsum: sum of the weights recorded at length n before this node;
@@ -403,6 +418,11 @@ __device__ __forceinline__ void grow_run(const RunDev &P, unsigned char *smem, c
     int frow = 0, fmaxn = 0;   // tour-sum row to flush at a part's end, and its depth
     bool do_flush = false, shared_flush = false;
     const uint32_t dq_mask = (1u << P.dq_log2cap) - 1u;
+    // a hand-over made in this iteration's node passes, copied after them
+    int don_cell = -1, don_bdp = 0;
+    uint32_t don_round = 0u;
+    // a donation cell: 32-byte header, the keys of sites 0..n_max, then their slots
+    const size_t cell_key_bytes = align16(((size_t)P.n_max + 1) * sizeof(Key));
     unsigned long long my_iters = 0ull;
     double *Wrow = P.Wn;
     unsigned long long *Srow = P.Sn;
@@ -546,10 +566,14 @@ __device__ __forceinline__ void grow_run(const RunDev &P, unsigned char *smem, c
                 base = __shfl_sync(kFull, base, leader);
                 take = __shfl_sync(kFull, take, leader);
                 const unsigned rk = __popc(hm & lt_mask);
-                if (idle && rk < take) {
-                    const unsigned long long pos = base + rk;
-                    const uint32_t cell = (uint32_t)pos & dq_mask;
-                    const uint32_t round = (uint32_t)(pos >> P.dq_log2cap);
+                bool claiming = idle && rk < take;
+                unsigned long long pos = 0ull;
+                uint32_t cell = 0u, round = 0u;
+                int cdp = -1;
+                if (claiming) {
+                    pos = base + rk;
+                    cell = (uint32_t)pos & dq_mask;
+                    round = (uint32_t)(pos >> P.dq_log2cap);
                     bool ok = false;
                     for (int spin = 0; spin < kCellSpin; ++spin) {
                         if (*(volatile unsigned int *)(P.dq_ready + cell) == round + 1u) { ok = true; break; }
@@ -558,62 +582,56 @@ __device__ __forceinline__ void grow_run(const RunDev &P, unsigned char *smem, c
                     if (!ok || pos + 1ull >= (1ull << 32)) {
                         set_status(P.status, ok ? PERM_EOVERFLOW : PERM_ETIMEOUT);
                         state = kDone;
+                        claiming = false;
                     } else {
                         __threadfence();
-                        const unsigned char *cb = P.dq_cells + (size_t)cell * (size_t)P.dq_cell_bytes;
-                        const uint4 h0 = __ldcg(reinterpret_cast<const uint4 *>(cb));
-                        const uint2 h1 = __ldcg(reinterpret_cast<const uint2 *>(cb + 16));
-                        const double cw = __longlong_as_double(__ldcg(reinterpret_cast<const long long *>(cb + 24)));
-                        const int dp = (int)h0.w;
-                        const uint32_t meta = h1.x;
-                        // the walk up to the branch point, site by site (Sec. 1); the keys
-                        // come in 16-byte vectors, four vectors in flight
-                        const uint4 *kv = reinterpret_cast<const uint4 *>(cb + 32);
-                        const int nv = (dp + kKeysPerVec<Key>) / kKeysPerVec<Key>;
-                        bool ovf = false;
-                        for (int v0 = 0; v0 < nv && !ovf; v0 += 4) {
-                            KeyVec<Key> buf[4];
-#pragma unroll
-                            for (int u = 0; u < 4; ++u)
-                                buf[u].v = (v0 + u < nv) ? __ldcg(kv + v0 + u) : make_uint4(0u, 0u, 0u, 0u);
-#pragma unroll
-                            for (int u = 0; u < 4; ++u) {
-#pragma unroll
-                                for (int e = 0; e < kKeysPerVec<Key>; ++e) {
-                                    const int k = (v0 + u) * kKeysPerVec<Key> + e;
-                                    if (k <= dp && !ovf) {
-                                        const int sl = hash_insert<Key>(hash, ST, lane, P.log2h, buf[u].k[e]);
-                                        if (sl < 0) ovf = true;
-                                        else sites[(uint32_t)k * ST + lane] = (uint16_t)sl;
-                                    }
-                                }
-                            }
-                        }
-                        __threadfence();
-                        *(volatile unsigned int *)(P.dq_free + cell) = round + 1u;
-                        if (ovf) { set_status(P.status, PERM_EOVERFLOW); state = kDone; }
-                        else {
-                            own = (int)h0.x; seq = h0.y; tour = h0.z;
-                            g = (unsigned long long)tour * (unsigned long long)P.n_seq + seq;
-                            did = (uint32_t)(pos + 1ull);
-                            ordinal = (unsigned long long)did << 32;
-                            donated = false; maxn = 0;
-                            top = 0; sbase = 0; bot = 0;
-                            const int cnt = (int)((meta >> 16) & 7u);
-                            const uint32_t dirs = meta >> 19;
-                            pend_dir = (int)(dirs & 7u);
-                            pend_w = cw;
-                            pend_depth = dp;
-                            if (cnt > 1) {
-                                smeta[lane] = (uint32_t)dp | ((uint32_t)(cnt - 1) << 16) | ((dirs >> 3) << 19);
-                                sw[lane] = cw;
-                                top = 1;
-                            }
-                            un_lo = dp + 1; un_hi = dp; tour_end = false;
-                            waiting = false;
-                            state = kUnwindState;      // resumes at the branch point below
-                        }
+                        cdp = (int)__ldcg(reinterpret_cast<const unsigned int *>(P.dq_cells + (size_t)cell *
+                                                                                (size_t)P.dq_cell_bytes) + 3);
                     }
+                }
+                // the walk up to the branch point (Sec. 1), each site straight into the
+                // slot it had in the donor's hash; the whole warp places one taker's
+                // sites at a time (the taker's hash is empty: it had no walk)
+                unsigned cm = __ballot_sync(kFull, claiming);
+                while (cm) {
+                    const int src = __ffs(cm) - 1;
+                    cm &= cm - 1u;
+                    const uint32_t scell = __shfl_sync(kFull, cell, src);
+                    const int sdp = __shfl_sync(kFull, cdp, src);
+                    const unsigned char *cb = P.dq_cells + (size_t)scell * (size_t)P.dq_cell_bytes;
+                    const Key *ck = reinterpret_cast<const Key *>(cb + 32);
+                    const uint16_t *cs = reinterpret_cast<const uint16_t *>(cb + 32 + cell_key_bytes);
+                    place_sites_from_cell<Key>(hash, sites, ST, src, sdp, ck, cs, lane);
+                }
+                __syncwarp();
+                if (claiming) {
+                    const unsigned char *cb = P.dq_cells + (size_t)cell * (size_t)P.dq_cell_bytes;
+                    const uint4 h0 = __ldcg(reinterpret_cast<const uint4 *>(cb));
+                    const uint2 h1 = __ldcg(reinterpret_cast<const uint2 *>(cb + 16));
+                    const double cw = __longlong_as_double(__ldcg(reinterpret_cast<const long long *>(cb + 24)));
+                    const int dp = (int)h0.w;
+                    const uint32_t meta = h1.x;
+                    __threadfence();
+                    *(volatile unsigned int *)(P.dq_free + cell) = round + 1u;
+                    own = (int)h0.x; seq = h0.y; tour = h0.z;
+                    g = (unsigned long long)tour * (unsigned long long)P.n_seq + seq;
+                    did = (uint32_t)(pos + 1ull);
+                    ordinal = (unsigned long long)did << 32;
+                    donated = false; maxn = 0;
+                    top = 0; sbase = 0; bot = 0;
+                    const int cnt = (int)((meta >> 16) & 7u);
+                    const uint32_t dirs = meta >> 19;
+                    pend_dir = (int)(dirs & 7u);
+                    pend_w = cw;
+                    pend_depth = dp;
+                    if (cnt > 1) {
+                        smeta[lane] = (uint32_t)dp | ((uint32_t)(cnt - 1) << 16) | ((dirs >> 3) << 19);
+                        sw[lane] = cw;
+                        top = 1;
+                    }
+                    un_lo = dp + 1; un_hi = dp; tour_end = false;
+                    waiting = false;
+                    state = kUnwindState;      // resumes at the branch point below
                 }
             }
             const int hcount = __popc(__ballot_sync(kFull, state == kNeed && (waiting || xbusy || exhausted)));
@@ -746,9 +764,11 @@ __device__ __forceinline__ void grow_run(const RunDev &P, unsigned char *smem, c
                     sites[(uint32_t)n * ST + lane] = (uint16_t)s0;
                 }
                 W = o.child_w;
-                if (snapshot && P.share && top - bot >= 2 && *(volatile int *)&head->want_don > 0) {
+                if (snapshot && P.share && don_cell < 0 && top - bot >= 2 && *(volatile int *)&head->want_don > 0) {
                     // hand the oldest waiting copy record to an idle walk: its subtree
-                    // grows there, and its weights still go to this tour's row `own`
+                    // grows there, and its weights still go to this tour's row `own`.
+                    // The header is written now; the walk's sites 0..bdp go into the
+                    // cell after the node passes, copied by the whole warp
                     const uint32_t bi = (uint32_t)(bot & (K - 1)) * ST + lane;
                     const uint32_t bm = bot < sbase ? gmeta[bot] : smeta[bi];
                     const double bw = bot < sbase ? gwt[bot] : sw[bi];
@@ -775,19 +795,9 @@ __device__ __forceinline__ void grow_run(const RunDev &P, unsigned char *smem, c
                             *reinterpret_cast<uint4 *>(cb) = make_uint4((uint32_t)own, seq, tour, (uint32_t)bdp);
                             *reinterpret_cast<uint2 *>(cb + 16) = make_uint2(bm, 0u);
                             *reinterpret_cast<double *>(cb + 24) = bw;
-                            uint4 *kv = reinterpret_cast<uint4 *>(cb + 32);
-                            const int nv = (bdp + kKeysPerVec<Key>) / kKeysPerVec<Key>;
-                            for (int v = 0; v < nv; ++v) {
-                                KeyVec<Key> buf;
-#pragma unroll
-                                for (int e = 0; e < kKeysPerVec<Key>; ++e) {
-                                    const int k = v * kKeysPerVec<Key> + e;
-                                    buf.k[e] = k <= bdp ? hash[(uint32_t)sites[(uint32_t)k * ST + lane] * ST + lane] : (Key)0;
-                                }
-                                kv[v] = buf.v;
-                            }
-                            __threadfence();
-                            *(volatile unsigned int *)(P.dq_ready + cell) = (uint32_t)(pos >> P.dq_log2cap) + 1u;
+                            don_cell = (int)cell;
+                            don_round = (uint32_t)(pos >> P.dq_log2cap);
+                            don_bdp = bdp;
                             bot += 1;
                             if (sbase < bot) sbase = bot;
                         } else {
@@ -838,6 +848,31 @@ __device__ __forceinline__ void grow_run(const RunDev &P, unsigned char *smem, c
                 state = kUnwindState;
             }
         }
+        }
+
+        // ---------------- hand-overs: the whole warp copies each donor's sites ----------------
+        // A donor's sites 0..bdp are still in its hash (this iteration's deletions come
+        // below), each in the slot an in-order rebuild would give it, so the cell holds
+        // (key, slot) per site and the taker places them without probing.
+        if (P.share) {
+            unsigned dm = __ballot_sync(kFull, don_cell >= 0);
+            if (dm) __syncwarp();          // every lane sees the donors' sites
+            while (dm) {
+                const int src = __ffs(dm) - 1;
+                dm &= dm - 1u;
+                const int scell = __shfl_sync(kFull, don_cell, src);
+                const int sbdp = __shfl_sync(kFull, don_bdp, src);
+                unsigned char *cb = P.dq_cells + (size_t)scell * (size_t)P.dq_cell_bytes;
+                Key *ck = reinterpret_cast<Key *>(cb + 32);
+                uint16_t *cs = reinterpret_cast<uint16_t *>(cb + 32 + cell_key_bytes);
+                copy_sites_to_cell<Key>(hash, sites, ST, src, sbdp, ck, cs, lane);
+                __syncwarp();
+                if (lane == src) {
+                    __threadfence();
+                    *(volatile unsigned int *)(P.dq_ready + scell) = don_round + 1u;
+                }
+            }
+            don_cell = -1;
         }
 
         // ---------------- backtrack: LIFO deletions, then resume ----------------

@@ -66,7 +66,7 @@ struct RunDev {
     int share_boost;               // ... once no tour of the run has finished for stall_ns
     long long stall_ns;
     int dq_log2cap;                // ring of 2^dq_log2cap donation cells
-    int dq_cell_bytes;             // header (32 bytes) + keys of sites 0..n_max, multiple of 16
+    int dq_cell_bytes;             // header (32 bytes) + keys and hash slots of sites 0..n_max
     unsigned char *dq_cells;
     unsigned long long *dq_head;   // donations taken
     unsigned long long *dq_tail;   // donations reserved
