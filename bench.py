@@ -560,7 +560,12 @@ def long_walks(cap_s=60.0):
     out = {"workload": "square lattice, n_max 10^4, 12 interacting sequences, from empty tables; "
                        "launches of 1, 2, 4, ... up to 16 tours per sequence", "cap_s": cap_s,
            "log_c10000_paper": LOG_C10000_PAPER, "launches": []}
-    run = pg.Run(2, n_max, N, 1, max_seconds=cap_s)
+    # the 12 sequences' tours grow on 12 walks, and helper walks (one walk per SM in
+    # all) grow their waiting copies: the start-up trees of reading 20 spread over
+    # the device while at most 12 tours are in flight, as with the paper's threads
+    helpers = max(0, sm_count() - N)
+    run = pg.Run(2, n_max, N, 1, max_seconds=cap_s, helper_walks=helpers)
+    out["helper_walks"] = helpers
     t0 = time.perf_counter()
     status, chunk = 0, 1
     while time.perf_counter() - t0 < cap_s:

@@ -47,7 +47,8 @@ class perm_config(C.Structure):
                 ("slots", C.c_int), ("lanes_per_warp", C.c_int), ("refresh_ns", C.c_int),
                 ("max_seconds", C.c_double), ("ramp_c0", C.c_int), ("ramp_gamma", C.c_double),
                 ("max_ctas", C.c_int), ("hash_scale", C.c_int), ("share_copies", C.c_int),
-                ("stack_ring", C.c_int), ("observables", C.c_int), ("walk_memory", C.c_int)]
+                ("stack_ring", C.c_int), ("observables", C.c_int), ("walk_memory", C.c_int),
+                ("helper_walks", C.c_int)]
 
 
 class perm_stats_t(C.Structure):

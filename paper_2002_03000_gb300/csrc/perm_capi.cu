@@ -33,6 +33,7 @@ struct perm_run_s {
     unsigned char *arena = nullptr;
     int ntab = 1;
     int xrows = 0;                 // tour-sum rows: one per walk, two with shared copies
+    int tour_slots = 0;            // walks that start tours; the other slots are helpers
     // device buffers
     double *Wn = nullptr, *Qn = nullptr, *X = nullptr, *gstk_w = nullptr, *Rn = nullptr;
     unsigned long long *Sn = nullptr, *tickets = nullptr, *seq_M = nullptr;
@@ -129,6 +130,7 @@ void perm_config_init(perm_config *cfg, int d, int n_max, int n_seq, uint64_t se
     cfg->stack_ring = 0;
     cfg->observables = 0;
     cfg->walk_memory = 0;
+    cfg->helper_walks = 0;
 }
 
 const char *perm_strerror(int code) {
@@ -169,6 +171,11 @@ int create_impl(perm_handle *out, const perm_config *cfg, const ForcedLayout *fo
     if (cfg->share_copies < -1 || cfg->share_copies > 1024) return PERM_EINVAL;
     if (cfg->observables != 0 && cfg->observables != 1) return PERM_EINVAL;
     if (cfg->walk_memory < 0 || cfg->walk_memory > 2) return PERM_EINVAL;
+    // helper walks take waiting copies only: they need shared copies
+    if (cfg->helper_walks < 0 || cfg->helper_walks > (1 << 20)) return PERM_EINVAL;
+    if (cfg->helper_walks > 0 && !(cfg->share_copies >= 0 && cfg->alg == PERM_ALG2 &&
+                                   cfg->threshold == PERM_THRESH_SNAPSHOT))
+        return PERM_EINVAL;
     if (cfg->stack_ring != 0 && cfg->stack_ring != 16 && cfg->stack_ring != 32 &&
         cfg->stack_ring != 64 && cfg->stack_ring != 128) return PERM_EINVAL;
     const int lpw = cfg->lanes_per_warp;
@@ -245,8 +252,9 @@ int create_impl(perm_handle *out, const perm_config *cfg, const ForcedLayout *fo
             h->num_sms = (int)std::max(1LL, std::min((long long)h->num_sms, need));
         }
     }
-    long long slots = cfg->slots ? cfg->slots : (long long)n_seq;
-    if (slots > n_seq) slots = n_seq;
+    long long tslots = cfg->slots ? cfg->slots : (long long)n_seq;   // walks that grow tours
+    if (tslots > n_seq) tslots = n_seq;
+    long long slots = tslots + (force ? 0 : cfg->helper_walks);      // and helper walks
     const long long slots_wanted = slots;
     int warps = 0, lanes = 0, stride = 0;
     if (force) {
@@ -292,6 +300,10 @@ int create_impl(perm_handle *out, const perm_config *cfg, const ForcedLayout *fo
         slots = slots_wanted < cap ? slots_wanted : cap;
     }
     h->ctas = (int)((slots + per_cta_eff - 1) / per_cta_eff);
+    // helpers are the walks beyond the tour walks (fewer when not all fit).  A batch
+    // member is laid out for the whole grid and its walks are granted per sequence by
+    // the batch kernel, so none of its walks is a helper by position
+    h->tour_slots = force ? (int)slots : (int)std::min(tslots, slots);
     h->worker_warps = warps;
     h->lanes = lanes;
     h->stride = stride;
@@ -389,7 +401,7 @@ static RunDev make_params(perm_handle h) {
     std::memset(&P, 0, sizeof(P));
     P.d = h->cfg.d; P.n_max = h->cfg.n_max; P.n_seq = h->cfg.n_seq; P.alg = h->cfg.alg;
     P.log2h = h->log2h; P.S = h->lanes; P.stride = h->stride;
-    P.worker_warps = h->worker_warps; P.slots = h->slots;
+    P.worker_warps = h->worker_warps; P.slots = h->slots; P.tour_slots = h->tour_slots;
     P.stack_cache = h->stack_cache;
     P.arena_mode = h->arena_mode; P.arena = h->arena; P.arena_cta_bytes = h->arena_cta_bytes;
     P.key0 = (uint32_t)h->cfg.seed ^ h->cfg.run_id;

@@ -412,7 +412,9 @@ __device__ __forceinline__ void grow_run(const RunDev &P, unsigned char *smem, c
     uint32_t did = 0u;
     bool donated = false;      // a part of this walk's own tour went to another walk
     bool xbusy = false;        // every tour-sum row of this walk is still used by such parts
-    bool exhausted = bl != nullptr && bl->helper;   // no tour tickets left (a helper takes none)
+    // no tour tickets left; a helper (of a batch, or a walk beyond the run's tour walks)
+    // takes none and grows waiting copies only
+    bool exhausted = (bl != nullptr && bl->helper) || sidx >= P.tour_slots;
     int my_hungry = 0;         // lane 0: this warp's share of P.hungry
     unsigned idle_ns = 500u;   // back-off of a warp with nothing to grow
     int frow = 0, fmaxn = 0;   // tour-sum row to flush at a part's end, and its depth

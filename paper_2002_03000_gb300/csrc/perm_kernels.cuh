@@ -22,6 +22,7 @@ struct RunDev {
     int stride;          // interleave stride of per-walk shared arrays (power of 2, >= S)
     int worker_warps;    // per CTA
     int slots;           // walks on the device
+    int tour_slots;      // walks that start tours (slots below it); the rest are helpers
     int stack_cache;     // stack records cached per walk in shared memory (power of 2)
     int arena_mode;      // ArenaMode
     long long arena_cta_bytes;     // bytes of one CTA's slice of the arena

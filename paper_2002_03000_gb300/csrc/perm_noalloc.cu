@@ -68,7 +68,8 @@ extern "C" int perm_run_static(const perm_config *cfg, int64_t tours_per_seq, do
     // walk memory) and shared copies (the run grows every copy on the walk that
     // made it)
     if (cfg->observables != 0 || cfg->hash_scale != 0 || cfg->lanes_per_warp != 0 ||
-        cfg->stack_ring != 0 || cfg->max_ctas != 0 || cfg->share_copies > 0 || cfg->walk_memory != 0)
+        cfg->stack_ring != 0 || cfg->max_ctas != 0 || cfg->share_copies > 0 || cfg->walk_memory != 0 ||
+        cfg->helper_walks != 0)
         return PERM_EUNSUPPORTED;
     const bool key64 = (d == 3 && n_max > 512);
     if (n_max > (d == 2 ? 32766 : (key64 ? (1 << 20) - 2 : 512))) return PERM_EUNSUPPORTED;
@@ -148,7 +149,7 @@ extern "C" int perm_run_static(const perm_config *cfg, int64_t tours_per_seq, do
     std::memset(&P, 0, sizeof(P));
     P.d = d; P.n_max = n_max; P.n_seq = n_seq; P.alg = PERM_ALG2;
     P.log2h = log2h; P.S = lanes; P.stride = stride; P.worker_warps = warps;
-    P.slots = (int)slots; P.stack_cache = K;
+    P.slots = (int)slots; P.tour_slots = (int)slots; P.stack_cache = K;
     P.key0 = (uint32_t)cfg->seed ^ cfg->run_id;
     P.key1 = (uint32_t)(cfg->seed >> 32);
     P.tour_limit = tours_per_seq * (long long)n_seq;

@@ -98,3 +98,38 @@ def test_share_cap_argument():
     for bad in (-2, 2000):
         with pytest.raises(pg.PermError):
             Run(2, 100, 64, 1, share_copies=bad)
+
+
+@pytest.mark.parametrize("d,n_max,N,helpers,tours", [(2, 200, 12, 300, 200), (3, 120, 12, 300, 200)])
+def test_helper_walks(d, n_max, N, helpers, tours, exact_counts):
+    """Walks beyond one per sequence start no tour and grow waiting copies only:
+    the tours are the sequences' own (M = N x tours, each finishing once), copies
+    move to the helpers, and the estimates meet exact c_n within 4.5 sigma; sampled
+    nodes of moved parts replay bit for bit in the oracle."""
+    torch_cuda()
+    seed = 17
+    with Run(d, n_max, N, seed, helper_walks=helpers) as run:
+        run.trace_enable(5, 1, 3000)
+        run.run(tours)
+        lc, S, rv = run.estimates()
+        st = run.stats()
+        count, recs, coords = run.trace_read()
+    M = N * tours
+    assert st["status"] == 0 and st["slots"] > N
+    assert st["tours"] == M and st["tours_finished"] == M and st["shared"] > 0
+    assert S[0] == M and S[1] == M
+    assert math.isclose(math.exp(lc[1]), 2 * d, rel_tol=1e-12)
+    top = 16 if d == 2 else 11
+    z = zscores(lc, rv, exact_counts[d][: top + 1])
+    assert np.all(np.abs(z[2:]) < 4.5), z
+    moved = [rec for rec in recs if (rec.ordinal >> 32) != 0]
+    assert moved
+    assert not replay(recs, coords, d, n_max, seed)
+
+
+def test_helper_walks_need_shared_copies():
+    import paper_2002_03000_gb300 as pg
+    torch_cuda()
+    for kw in (dict(share_copies=-1), dict(threshold=pg.PERM_THRESH_FRESH), dict(alg=pg.PERM_ALG1)):
+        with pytest.raises(pg.PermError):
+            Run(2, 32, 4, 1, helper_walks=8, **kw)
