@@ -103,9 +103,11 @@ typedef struct {
     int helper_walks;  /* walks beyond one per sequence that start no tour and grow
                           waiting copies of the sequences' tours only (shared copies,
                           Sec. 2: copies grow independently); at most N tours are in
-                          flight whatever their number.  Needs Algorithm 2 with
-                          snapshot thresholds and shared copies on; 0 = none (default).
-                          Fewer run when not all fit */
+                          flight whatever their number.  k > 0 needs Algorithm 2 with
+                          snapshot thresholds and shared copies on; 0 = none; -1
+                          (default) = the walks the automatic layout has room for
+                          beyond the tour walks (up to 4 warps of 8 per SM) when
+                          shared copies are on, else none.  Fewer run when not all fit */
 } perm_config;
 
 /* Fill cfg with defaults for (d, n_max, n_seq, seed). */
@@ -359,8 +361,8 @@ int perm_autotune(perm_config *cfg, int64_t probe_tours);
  * whose scratch exceeds the buffer is rejected with PERM_ESCRATCH.  The run
  * grows every waiting copy on the walk that made it (no shared copies:
  * share_copies 0 or -1 both mean that here) and uses the automatic layout;
- * observables, hash_scale, lanes_per_warp, stack_ring, max_ctas, walk_memory,
- * helper_walks other than 0, or share_copies > 0, return PERM_EUNSUPPORTED (every walk's
+ * observables, hash_scale, lanes_per_warp, stack_ring, max_ctas, walk_memory
+ * other than 0, helper_walks > 0 or share_copies > 0 return PERM_EUNSUPPORTED (every walk's
  * state must then fit in shared memory).  Starts from empty tables and
  * grows tours_per_seq tours of each of cfg->n_seq sequences (M = n_seq *
  * tours_per_seq).

@@ -130,7 +130,7 @@ void perm_config_init(perm_config *cfg, int d, int n_max, int n_seq, uint64_t se
     cfg->stack_ring = 0;
     cfg->observables = 0;
     cfg->walk_memory = 0;
-    cfg->helper_walks = 0;
+    cfg->helper_walks = -1;
 }
 
 const char *perm_strerror(int code) {
@@ -172,7 +172,7 @@ int create_impl(perm_handle *out, const perm_config *cfg, const ForcedLayout *fo
     if (cfg->observables != 0 && cfg->observables != 1) return PERM_EINVAL;
     if (cfg->walk_memory < 0 || cfg->walk_memory > 2) return PERM_EINVAL;
     // helper walks take waiting copies only: they need shared copies
-    if (cfg->helper_walks < 0 || cfg->helper_walks > (1 << 20)) return PERM_EINVAL;
+    if (cfg->helper_walks < -1 || cfg->helper_walks > (1 << 20)) return PERM_EINVAL;
     if (cfg->helper_walks > 0 && !(cfg->share_copies >= 0 && cfg->alg == PERM_ALG2 &&
                                    cfg->threshold == PERM_THRESH_SNAPSHOT))
         return PERM_EINVAL;
@@ -254,7 +254,13 @@ int create_impl(perm_handle *out, const perm_config *cfg, const ForcedLayout *fo
     }
     long long tslots = cfg->slots ? cfg->slots : (long long)n_seq;   // walks that grow tours
     if (tslots > n_seq) tslots = n_seq;
-    long long slots = tslots + (force ? 0 : cfg->helper_walks);      // and helper walks
+    // and helper walks: as asked, or (-1) the walks the automatic layout has room for
+    // beyond the tour walks (4 warps of 8 per SM), when shared copies are on
+    const bool can_help = cfg->share_copies >= 0 && cfg->alg == PERM_ALG2 &&
+                          cfg->threshold == PERM_THRESH_SNAPSHOT && !force;
+    long long helpers = cfg->helper_walks;
+    if (helpers < 0) helpers = can_help && !lpw ? std::max(0LL, (long long)h->num_sms * 32 - tslots) : 0;
+    long long slots = tslots + helpers;
     const long long slots_wanted = slots;
     int warps = 0, lanes = 0, stride = 0;
     if (force) {

@@ -69,7 +69,7 @@ extern "C" int perm_run_static(const perm_config *cfg, int64_t tours_per_seq, do
     // made it)
     if (cfg->observables != 0 || cfg->hash_scale != 0 || cfg->lanes_per_warp != 0 ||
         cfg->stack_ring != 0 || cfg->max_ctas != 0 || cfg->share_copies > 0 || cfg->walk_memory != 0 ||
-        cfg->helper_walks != 0)
+        cfg->helper_walks > 0)
         return PERM_EUNSUPPORTED;
     const bool key64 = (d == 3 && n_max > 512);
     if (n_max > (d == 2 ? 32766 : (key64 ? (1 << 20) - 2 : 512))) return PERM_EUNSUPPORTED;

@@ -133,3 +133,9 @@ def test_helper_walks_need_shared_copies():
     for kw in (dict(share_copies=-1), dict(threshold=pg.PERM_THRESH_FRESH), dict(alg=pg.PERM_ALG1)):
         with pytest.raises(pg.PermError):
             Run(2, 32, 4, 1, helper_walks=8, **kw)
+        with Run(2, 32, 4, 1, **kw) as run:          # the default adds none there
+            assert run.stats()["slots"] == 4
+    with Run(2, 32, 4, 1, helper_walks=0) as run:
+        assert run.stats()["slots"] == 4
+    with Run(2, 32, 4, 1) as run:                    # default: the layout's spare walks
+        assert run.stats()["slots"] > 4

@@ -121,7 +121,8 @@ def test_static_run_refuses_settings_it_does_not_carry_out():
     S = torch.zeros(L, dtype=torch.int64, device="cuda")
     Q = torch.zeros(L, dtype=torch.float64, device="cuda")
     for field, value in (("observables", 1), ("hash_scale", 1), ("lanes_per_warp", 4),
-                         ("stack_ring", 64), ("max_ctas", 8), ("share_copies", 4), ("walk_memory", 2)):
+                         ("stack_ring", 64), ("max_ctas", 8), ("share_copies", 4), ("walk_memory", 2),
+                         ("helper_walks", 8)):
         cfg = nat.perm_config_init(2, 16, 4, 1)
         setattr(cfg, field, value)
         with pytest.raises(nat.PermError) as e:
