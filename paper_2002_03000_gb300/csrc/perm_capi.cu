@@ -192,7 +192,7 @@ int create_impl(perm_handle *out, const perm_config *cfg, const ForcedLayout *fo
     if (!h) return PERM_ENOMEM;
     h->cfg = *cfg;
     if (cfg->stack_ring) h->stack_cache = cfg->stack_ring;
-    if (h->cfg.refresh_ns == 0) h->cfg.refresh_ns = 4000;
+    if (h->cfg.refresh_ns == 0) h->cfg.refresh_ns = 8000;
     if (h->cfg.refresh_ns > 1000000) h->cfg.refresh_ns = 1000000;
     if (h->cfg.max_seconds == 0.0) h->cfg.max_seconds = 600.0;
     if (h->cfg.ramp_c0 == 0) h->cfg.ramp_c0 = 2;

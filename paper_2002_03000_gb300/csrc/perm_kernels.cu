@@ -38,6 +38,7 @@ constexpr int kUnwind = 8;         // hash deletions per walk per iteration
 constexpr int kNodePasses = 2;     // nodes a walk may grow per iteration
 constexpr int kPoolExtra = 4;      // extra tour tickets fetched per warp (snapshot)
 constexpr int kChunk = 8;          // stack records moved per spill or fill (ring >= 2 kChunk)
+constexpr int kReloadBatch = 8;    // snapshot entries a refresher lane loads before storing them
 constexpr unsigned kRowFree = 0xFFFFFFFFu;   // outst: the walk's tour-sum row is unused
 constexpr int kMinShareGap = 8;    // share a waiting copy only if it may still grow this many steps
 constexpr int kCellSpin = 1 << 20; // bounded wait for a donation cell being written
@@ -64,6 +65,15 @@ __device__ __forceinline__ long long global_ns() {
     long long t;
     asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
     return t;
+}
+
+// A load of a table entry that other SMs update with atomics: an aligned 8-byte
+// load is single-copy atomic; relaxed at GPU scope, so the loads of one batch
+// stay in flight together.
+__device__ __forceinline__ double ld_relaxed(const double *p) {
+    double v;
+    asm volatile("ld.relaxed.gpu.global.f64 %0, [%1];" : "=d"(v) : "l"(p));
+    return v;
 }
 
 __device__ __forceinline__ void set_status(int *status, int code) {
@@ -312,6 +322,7 @@ __device__ __forceinline__ void grow_run(const RunDev &P, unsigned char *smem, c
         long long t_change = t0;
         if (lane == 0) *(volatile int *)&head->cap = P.share;
         for (long long it = 0;; ++it) {
+            const long long c_it = clock64();
             const int done = __shfl_sync(kFull, *(volatile int *)&head->done_warps, 0);
             __threadfence_block();
             if (done >= P.worker_warps) {
@@ -320,8 +331,19 @@ __device__ __forceinline__ void grow_run(const RunDev &P, unsigned char *smem, c
             }
             unsigned long long Ms = *(volatile unsigned long long *)P.tickets;
             if ((long long)Ms > limit) Ms = (unsigned long long)limit;
-            for (int k = lane; k < L; k += 32)
-                *(volatile double *)&Wsnap[k] = *(volatile double *)(P.Wn + k);
+            for (int k0 = 0; k0 < L; k0 += 32 * kReloadBatch) {
+                double v[kReloadBatch];
+#pragma unroll
+                for (int j = 0; j < kReloadBatch; ++j) {
+                    const int k = k0 + j * 32 + lane;
+                    v[j] = k < L ? ld_relaxed(P.Wn + k) : 0.0;
+                }
+#pragma unroll
+                for (int j = 0; j < kReloadBatch; ++j) {
+                    const int k = k0 + j * 32 + lane;
+                    if (k < L) *(volatile double *)&Wsnap[k] = v[j];
+                }
+            }
             if (lane == 0) *(volatile unsigned long long *)&head->Ms = Ms;
             if (P.share && lane == 0) {
                 // idle walks not yet served by a queued copy, split over the CTAs
@@ -355,7 +377,14 @@ __device__ __forceinline__ void grow_run(const RunDev &P, unsigned char *smem, c
                 }
             }
             __syncwarp();
-            __nanosleep((unsigned)P.refresh_ns);
+            // one reload per refresh period, paced on the SM's cycle counter at two
+            // cycles per ns (the 2 GHz SM clock): one __nanosleep may end well before
+            // or after the time it is given
+            for (int nap = 0; nap < 256; ++nap) {
+                const long long left = __shfl_sync(kFull, (c_it + 2ll * P.refresh_ns - clock64()) >> 1, 0);
+                if (left <= 0) break;
+                __nanosleep((unsigned)(left < 1000 ? left : 1000));
+            }
             const bool late = (it & 15) == 0 && global_ns() - t0 > P.max_ns;
             if (__any_sync(kFull, late)) {
                 if (lane == 0) set_status(P.status, PERM_ETIMEOUT);

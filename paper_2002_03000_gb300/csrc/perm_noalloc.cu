@@ -153,7 +153,7 @@ extern "C" int perm_run_static(const perm_config *cfg, int64_t tours_per_seq, do
     P.key0 = (uint32_t)cfg->seed ^ cfg->run_id;
     P.key1 = (uint32_t)(cfg->seed >> 32);
     P.tour_limit = tours_per_seq * (long long)n_seq;
-    P.refresh_ns = cfg->refresh_ns ? (cfg->refresh_ns > 1000000 ? 1000000 : cfg->refresh_ns) : 4000;
+    P.refresh_ns = cfg->refresh_ns ? (cfg->refresh_ns > 1000000 ? 1000000 : cfg->refresh_ns) : 8000;
     P.max_ns = (long long)((cfg->max_seconds > 0.0 ? cfg->max_seconds : 600.0) * 1e9);
     P.Wn = W_n; P.Sn = S_n; P.Qn = Q_n;
     P.tickets = cnt + 0; P.seq_M = nullptr;
