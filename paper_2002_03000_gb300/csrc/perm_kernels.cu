@@ -162,7 +162,7 @@ __device__ __forceinline__ NodeOut grow_node(const Key *hash, int stride, int la
                                              unsigned long long M, unsigned long long ordinal,
                                              uint32_t seq, uint32_t tour, uint32_t k0, uint32_t k1,
                                              const double *aoc, int (&eslot)[2 * D],
-                                             const Cutoffs &cuts, bool force_exact = false) {
+                                             const Cutoffs &cuts, double invM = 0.0, bool force_exact = false) {
     NodeOut o;
     o.a = 0; o.mask = 0; o.c = 0; o.dirs = 0u; o.child_w = 0.0; o.overflow = false; o.exact = false;
     // three independent chains: the node's random block, the estimate of r, and the probes
@@ -222,11 +222,18 @@ __device__ __forceinline__ NodeOut grow_node(const Key *hash, int stride, int la
             o.exact = true;
             if (surv) o.child_w = __dmul_rn(__dmul_rn(W, __ddiv_rn(1.0, R)), a_sc);
             else if (c > 0) o.child_w = __dmul_rn(__ddiv_rn(W, (double)c), a_sc);
-        } else if (surv) {
-            // a survivor carries W/r = [W_n]^sample = (Wsum + W)/M
-            o.child_w = __dmul_rn(__ddiv_rn(__dadd_rn(Wsum, W), __ull2double_rn(M)), a_sc);
-        } else if (c > 0) {
-            o.child_w = __dmul_rn(W, row[a * 8 + c]);    // (W/c) a_+ 2^-dE
+        } else {
+            // a survivor carries W/r = [W_n]^sample = (Wsum + W)/M, a child of an
+            // enrichment (W/c) a_+ 2^-dE: one double-precision product for both.
+            // invM (when nonzero) is 1/M rounded to double, so the survivor's weight
+            // is within 2^-51 (relative) of the quotient
+            double base = W, fac = row[a * 8 + c];
+            if (surv) {
+                const double s = __dadd_rn(Wsum, W);
+                base = invM != 0.0 ? __dmul_rn(s, invM) : __ddiv_rn(s, __ull2double_rn(M));
+                fac = a_sc;
+            }
+            o.child_w = __dmul_rn(base, fac);
         }
     }
     if (c == 0) { o.outcome = kPruned; o.child_w = 0.0; return o; }
@@ -455,6 +462,8 @@ __device__ __forceinline__ void grow_run(const RunDev &P, unsigned char *smem, c
     // a donation cell: 32-byte header, the keys of sites 0..n_max, then their slots
     const size_t cell_key_bytes = align16(((size_t)P.n_max + 1) * sizeof(Key));
     unsigned long long my_iters = 0ull;
+    unsigned long long inv_of = 0ull;   // the snapshot M whose reciprocal inv_ms holds
+    double inv_ms = 0.0;
     double *Wrow = P.Wn;
     unsigned long long *Srow = P.Sn;
     double *Rrow = P.Rn;
@@ -693,6 +702,13 @@ __device__ __forceinline__ void grow_run(const RunDev &P, unsigned char *smem, c
         // nodes; a walk that reached a leaf waits for the backtrack below.
         for (int pass = 0; pass < kNodePasses; ++pass) {
         if (pass > 0 && !__any_sync(kFull, state == kNode)) break;
+        // the snapshot's M for this pass, and its reciprocal (taken by the whole warp
+        // once per new snapshot: double-precision arithmetic is slow on this part)
+        unsigned long long Ms_p = 0ull;
+        if (snapshot) {
+            Ms_p = __shfl_sync(kFull, *(volatile unsigned long long *)&head->Ms, 0);
+            if (Ms_p != inv_of) { inv_of = Ms_p; inv_ms = __drcp_rn(__ull2double_rn(Ms_p)); }
+        }
         if (state == kNode) {
             // the sum of the weights recorded at this length before the node (a
             // snapshot, or the global table's value returned by the node's own add)
@@ -704,8 +720,7 @@ __device__ __forceinline__ void grow_run(const RunDev &P, unsigned char *smem, c
                 atomicAdd(P.Wn + n, W);
                 atomicAdd(P.Sn + n, 1ull);
                 Wsum = *(volatile double *)&Wsnap[n];
-                const unsigned long long Ms = *(volatile unsigned long long *)&head->Ms;
-                Mb = Ms > g + 1ull ? Ms : g + 1ull;
+                Mb = Ms_p > g + 1ull ? Ms_p : g + 1ull;
             } else {
                 Wsum = atomicAdd(&Wrow[n], W);
                 atomicAdd(&Srow[n], 1ull);
@@ -730,7 +745,8 @@ __device__ __forceinline__ void grow_run(const RunDev &P, unsigned char *smem, c
 #pragma unroll
             for (int j = 0; j < 2 * D; ++j) eslot[j] = 0;
             const NodeOut o = grow_node<D, Key>(hash, ST, lane, P.log2h, n, P.n_max, cx, cy, cz, W, Wsum,
-                                                Mb, ordinal, seq, tour, P.key0, P.key1, aoc, eslot, cuts);
+                                                Mb, ordinal, seq, tour, P.key0, P.key1, aoc, eslot, cuts,
+                                                (snapshot && Mb == Ms_p) ? inv_ms : 0.0);
             if (o.overflow) set_status(P.status, PERM_EOVERFLOW);
             my_exact += o.exact ? 1ull : 0ull;
 
@@ -1207,7 +1223,7 @@ __global__ void __launch_bounds__(32) debug_step_kernel(int n_max, int log2h, in
     const Cutoffs none{nullptr, 1, 1.0, 1.0, 0ull};
     const NodeOut o = grow_node<D, Key>(hash, kStride, lane, log2h, n, n_max, cx, cy, cz, Wv[b],
                                         Wsv[b], Mv[b], ordv[b], seqv[b], tourv[b], k0, k1, aoc, eslot,
-                                        none, force_exact != 0);
+                                        none, 0.0, force_exact != 0);
     oi[0] = (ovf || o.overflow) ? -2 : o.outcome;
     oi[1] = o.a;
     oi[2] = o.mask;
