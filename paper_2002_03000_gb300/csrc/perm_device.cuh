@@ -125,7 +125,7 @@ __device__ __forceinline__ int hash_insert(Key *tab, int S, int lane, int log2h,
 template <int D, typename Key>
 __device__ __forceinline__ int probe_neighbours(const Key *tab, int S, int lane, int log2h,
                                                 int x, int y, int z, int (&slot)[2 * D],
-                                                bool &overflow) {
+                                                bool &overflow, int back = -1) {
     const uint32_t mask = (1u << log2h) - 1u;
     Key key[2 * D];
     uint32_t s[2 * D];
@@ -137,7 +137,9 @@ __device__ __forceinline__ int probe_neighbours(const Key *tab, int S, int lane,
         s[j] = hash_home(key[j], log2h);
         slot[j] = 0;
     }
-    uint32_t pending = (1u << (2 * D)) - 1u, freem = 0u;
+    // direction `back` leads to the walk's previous site, occupied by definition:
+    // no probe
+    uint32_t pending = ((1u << (2 * D)) - 1u) & ~(back >= 0 ? 1u << back : 0u), freem = 0u;
     for (int it = 0; it <= (int)mask; ++it) {
         Key v[2 * D];
 #pragma unroll
@@ -182,7 +184,10 @@ __device__ __forceinline__ int probe_neighbours(const Key *tab, int S, int lane,
 // |x - r| <= 10.02 2^-24 x.  Every margin below allows at least 15 2^-24 x.
 // Doubles with no such bound (W zero, negative, subnormal or not finite; Wsum
 // negative, subnormal or not finite; Wsum/W above 2^100) set `odd` and take
-// the exact path.
+// the exact path, and so does M of 2^32 or more (M enters through a 32-bit
+// conversion: a 64-bit one costs as much as a double-precision operation).
+// Every operation here is single-precision or integer arithmetic: a double-
+// precision one takes 64 cycles or more on this part.
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ uint32_t mant24_bits(unsigned long long b, int &ef) {
     const uint32_t hi = (uint32_t)(b >> 32) & 0xFFFFFu, lo = (uint32_t)b;
@@ -217,8 +222,8 @@ __device__ __forceinline__ float ratio_estimate(double W, double Wsum, unsigned 
     float rho = __fmul_rn(q, __uint_as_float((uint32_t)(e + 127) << 23));   // exact scaling
     rho = s_zero ? 0.0f : rho;
     const float s = __fadd_rn(1.0f, rho);
-    const float Mf = (M >> 32) ? __ull2float_rn(M) : __uint2float_rn((uint32_t)M);
-    odd = bad;
+    const float Mf = __uint2float_rn((uint32_t)M);
+    odd = bad || (M >> 32) != 0ull;
     return __fmul_rn(Mf, rcp_approx(s));
 }
 

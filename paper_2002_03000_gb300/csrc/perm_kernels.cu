@@ -162,7 +162,8 @@ __device__ __forceinline__ NodeOut grow_node(const Key *hash, int stride, int la
                                              unsigned long long M, unsigned long long ordinal,
                                              uint32_t seq, uint32_t tour, uint32_t k0, uint32_t k1,
                                              const double *aoc, int (&eslot)[2 * D],
-                                             const Cutoffs &cuts, double invM = 0.0, bool force_exact = false) {
+                                             const Cutoffs &cuts, double invM = 0.0, int back = -1,
+                                             bool force_exact = false) {
     NodeOut o;
     o.a = 0; o.mask = 0; o.c = 0; o.dirs = 0u; o.child_w = 0.0; o.overflow = false; o.exact = false;
     // three independent chains: the node's random block, the estimate of r, and the probes
@@ -172,7 +173,7 @@ __device__ __forceinline__ NodeOut grow_node(const Key *hash, int stride, int la
     o.r = n == 0 ? 1.0 : widen(x);
     if (n == n_max) { o.outcome = kLeafNmax; return o; }
     bool ovf = false;
-    const int fm = probe_neighbours<D, Key>(hash, stride, lane, log2h, cx, cy, cz, eslot, ovf);
+    const int fm = probe_neighbours<D, Key>(hash, stride, lane, log2h, cx, cy, cz, eslot, ovf, back);
     o.overflow = ovf;
     o.mask = fm;
     const int a = __popc(fm);
@@ -225,13 +226,15 @@ __device__ __forceinline__ NodeOut grow_node(const Key *hash, int stride, int la
         } else {
             // a survivor carries W/r = [W_n]^sample = (Wsum + W)/M, a child of an
             // enrichment (W/c) a_+ 2^-dE: one double-precision product for both.
-            // invM (when nonzero) is 1/M rounded to double, so the survivor's weight
-            // is within 2^-51 (relative) of the quotient
+            // invM (when nonzero) is 1/M rounded to double; the survivor's factor
+            // (1/M) a_+ 2^-dE is formed beside the sum Wsum + W, so that its weight
+            // (within 2^-51 of the quotient, relative) takes two dependent double
+            // operations.  The tests of invM and of the outcome are integer ones
             double base = W, fac = row[a * 8 + c];
             if (surv) {
-                const double s = __dadd_rn(Wsum, W);
-                base = invM != 0.0 ? __dmul_rn(s, invM) : __ddiv_rn(s, __ull2double_rn(M));
-                fac = a_sc;
+                base = __dadd_rn(Wsum, W);
+                if (__double_as_longlong(invM) != 0ll) fac = __dmul_rn(invM, a_sc);
+                else { base = __ddiv_rn(base, __ull2double_rn(M)); fac = a_sc; }
             }
             o.child_w = __dmul_rn(base, fac);
         }
@@ -430,6 +433,7 @@ __device__ __forceinline__ void grow_run(const RunDev &P, unsigned char *smem, c
     uint32_t seq = 0u, tour = 0u;
     int top = 0, sbase = 0;
     int un_lo = 0, un_hi = -1, pend_dir = 0, pend_depth = 0;
+    int back = -1;             // the direction from the end-point to the previous site (-1: empty walk)
     bool tour_end = false;
     double pend_w = 0.0;
     unsigned long long my_steps = 0ull, my_copies = 0ull, my_exact = 0ull;
@@ -575,7 +579,7 @@ __device__ __forceinline__ void grow_run(const RunDev &P, unsigned char *smem, c
             }
             if (state == kNeed && !waiting && !xbusy && !exhausted && (P.alg == PERM_ALG2 || cur_seq >= 0)) {
                 // start a tour at the empty walk (Sec. 1: W(empty) = 1)
-                n = 0; cx = cy = cz = 0; maxn = 0; W = 1.0; ordinal = 0ull;
+                n = 0; cx = cy = cz = 0; maxn = 0; W = 1.0; ordinal = 0ull; back = -1;
                 top = 0; sbase = 0; bot = 0;
                 own = myrow; did = 0u; donated = false;
                 const int s0 = hash_insert<Key>(hash, ST, lane, P.log2h,
@@ -746,7 +750,7 @@ __device__ __forceinline__ void grow_run(const RunDev &P, unsigned char *smem, c
             for (int j = 0; j < 2 * D; ++j) eslot[j] = 0;
             const NodeOut o = grow_node<D, Key>(hash, ST, lane, P.log2h, n, P.n_max, cx, cy, cz, W, Wsum,
                                                 Mb, ordinal, seq, tour, P.key0, P.key1, aoc, eslot, cuts,
-                                                (snapshot && Mb == Ms_p) ? inv_ms : 0.0);
+                                                (snapshot && Mb == Ms_p) ? inv_ms : 0.0, back);
             if (o.overflow) set_status(P.status, PERM_EOVERFLOW);
             my_exact += o.exact ? 1ull : 0ull;
 
@@ -805,6 +809,7 @@ __device__ __forceinline__ void grow_run(const RunDev &P, unsigned char *smem, c
                 const int dir0 = (int)(o.dirs & 7u);
                 const int s0 = select_slot<D>(eslot, dir0);
                 step_coords(dir0, cx, cy, cz);
+                back = dir0 ^ 1;
                 n += 1;
                 if (n < P.n_max) {
                     hash[(uint32_t)s0 * ST + lane] = KeyCodec<D, Key>::encode(cx, cy, cz);
@@ -937,6 +942,7 @@ __device__ __forceinline__ void grow_run(const RunDev &P, unsigned char *smem, c
                     const int dp = pend_depth;
                     KeyCodec<D, Key>::decode(hash[(uint32_t)sites[(uint32_t)dp * ST + lane] * ST + lane], cx, cy, cz);
                     step_coords(pend_dir, cx, cy, cz);
+                    back = pend_dir ^ 1;
                     n = dp + 1;
                     if (n < P.n_max) {
                         const int s = hash_insert<Key>(hash, ST, lane, P.log2h, KeyCodec<D, Key>::encode(cx, cy, cz));
@@ -994,7 +1000,7 @@ __device__ __forceinline__ void grow_run(const RunDev &P, unsigned char *smem, c
 #pragma unroll
                     for (int u = 0; u < 8; ++u) {
                         const int k = k0 + u * 32 + lane;
-                        if (x[u] != 0.0) {
+                        if (__double_as_longlong(x[u]) != 0ll) {     // (an integer test: no -0.0 here)
                             atomicAdd(&Qr[k], __dmul_rn(x[u], x[u]));
                             __stcg(Xr + k, 0.0);
                         }
@@ -1223,7 +1229,7 @@ __global__ void __launch_bounds__(32) debug_step_kernel(int n_max, int log2h, in
     const Cutoffs none{nullptr, 1, 1.0, 1.0, 0ull};
     const NodeOut o = grow_node<D, Key>(hash, kStride, lane, log2h, n, n_max, cx, cy, cz, Wv[b],
                                         Wsv[b], Mv[b], ordv[b], seqv[b], tourv[b], k0, k1, aoc, eslot,
-                                        none, 0.0, force_exact != 0);
+                                        none, 0.0, -1, force_exact != 0);
     oi[0] = (ovf || o.overflow) ? -2 : o.outcome;
     oi[1] = o.a;
     oi[2] = o.mask;
