@@ -104,10 +104,13 @@ typedef struct {
                           waiting copies of the sequences' tours only (shared copies,
                           Sec. 2: copies grow independently); at most N tours are in
                           flight whatever their number.  k > 0 needs Algorithm 2 with
-                          snapshot thresholds and shared copies on; 0 = none; -1
-                          (default) = the walks the automatic layout has room for
+                          snapshot thresholds and shared copies on; 0 (default) =
+                          none; -1 = the walks the automatic layout has room for
                           beyond the tour walks (up to 4 warps of 8 per SM) when
-                          shared copies are on, else none.  Fewer run when not all fit */
+                          shared copies are on, else none.  Fewer run when not all
+                          fit.  They pay off for long walks from few sequences
+                          (n_max 10^4 from 12); with many sequences or short walks
+                          they gain nothing or cost time */
 } perm_config;
 
 /* Fill cfg with defaults for (d, n_max, n_seq, seed). */

@@ -15,7 +15,7 @@ class Run:
     def __init__(self, d, n_max, n_seq, seed, run_id=0, alg=PERM_ALG2,
                  threshold=PERM_THRESH_SNAPSHOT, slots=0, lanes_per_warp=0, refresh_ns=0,
                  max_seconds=0.0, ramp_c0=0, ramp_gamma=0.0, max_ctas=0, hash_scale=0,
-                 share_copies=0, stack_ring=0, observables=0, walk_memory=0, helper_walks=-1):
+                 share_copies=0, stack_ring=0, observables=0, walk_memory=0, helper_walks=0):
         cfg = _native.perm_config_init(d, n_max, n_seq, seed)
         cfg.run_id = run_id
         cfg.alg = alg

@@ -130,7 +130,7 @@ void perm_config_init(perm_config *cfg, int d, int n_max, int n_seq, uint64_t se
     cfg->stack_ring = 0;
     cfg->observables = 0;
     cfg->walk_memory = 0;
-    cfg->helper_walks = -1;
+    cfg->helper_walks = 0;
 }
 
 const char *perm_strerror(int code) {
@@ -254,8 +254,9 @@ int create_impl(perm_handle *out, const perm_config *cfg, const ForcedLayout *fo
     }
     long long tslots = cfg->slots ? cfg->slots : (long long)n_seq;   // walks that grow tours
     if (tslots > n_seq) tslots = n_seq;
-    // and helper walks: as asked, or (-1) the walks the automatic layout has room for
-    // beyond the tour walks (4 warps of 8 per SM), when shared copies are on
+    // and helper walks: as asked (none by default), or (-1) the walks the automatic
+    // layout has room for beyond the tour walks (4 warps of 8 per SM), when shared
+    // copies are on
     const bool can_help = cfg->share_copies >= 0 && cfg->alg == PERM_ALG2 &&
                           cfg->threshold == PERM_THRESH_SNAPSHOT && !force;
     long long helpers = cfg->helper_walks;

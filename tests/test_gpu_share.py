@@ -139,3 +139,18 @@ def test_helper_walks_need_shared_copies():
         assert run.stats()["slots"] == 4
     with Run(2, 32, 4, 1) as run:                    # default: the layout's spare walks
         assert run.stats()["slots"] > 4
+
+
+def test_helper_walks_default_none_and_fill_option():
+    """No helper walks unless asked; helper_walks = -1 fills the automatic layout's
+    room beyond the tour walks, and every tour still finishes once."""
+    torch_cuda()
+    with Run(2, 64, 12, 3) as run:
+        run.run(4)
+        plain = run.stats()
+    with Run(2, 64, 12, 3, helper_walks=-1) as run:
+        run.run(4)
+        filled = run.stats()
+    assert plain["status"] == 0 and filled["status"] == 0
+    assert plain["slots"] == 12 and filled["slots"] > 12
+    assert plain["tours_finished"] == filled["tours_finished"] == 48
