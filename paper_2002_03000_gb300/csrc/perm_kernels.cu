@@ -275,7 +275,11 @@ constexpr int kStalledBit = 4;
 // The growth of one run by one CTA (Secs. 1-3): the refresher warp and the walk
 // warps.  A single-run launch calls it once (bl == nullptr: the CTA stays until
 // the run is complete); a batch launch calls it for each run a CTA joins.
-template <int D, typename Key, int MODE>
+// SHARED: every region is in shared memory (no arena), known at compile time, so
+// that the walks' hashes, site lists and stacks are reached by shared-memory
+// instructions rather than generic ones (a generic load that lands in shared
+// memory waits longer, and in the long-scoreboard queue).
+template <int D, typename Key, int MODE, bool SHARED>
 __device__ __forceinline__ void grow_run(const RunDev &P, unsigned char *smem, const BatchLeave *bl,
                                          int cta_walks) {
     const int L = P.n_max + 1;
@@ -293,7 +297,7 @@ __device__ __forceinline__ void grow_run(const RunDev &P, unsigned char *smem, c
     const size_t hbytes = head_region_bytes(P.n_max, snapshot);
     const size_t wbytes = warp_region_bytes(P.n_max, P.log2h, K, sizeof(Key), ST);
     unsigned char *hbase = smem, *wbase = smem + hbytes;
-    if (P.arena_mode != kArenaNone) {
+    if (!SHARED && P.arena_mode != kArenaNone) {
         unsigned char *a = P.arena + (size_t)blockIdx.x * (size_t)P.arena_cta_bytes;
         if (P.arena_mode == kArenaAll) { hbase = a; wbase = a + hbytes; }
         else wbase = a;
@@ -1055,7 +1059,8 @@ __device__ __forceinline__ void grow_run(const RunDev &P, unsigned char *smem, c
 template <int D, typename Key, int MODE>
 __global__ void __launch_bounds__(32 * 9, 1) grow_kernel(const __grid_constant__ RunDev P) {
     extern __shared__ __align__(16) unsigned char smem[];
-    grow_run<D, Key, MODE>(P, smem, nullptr, P.worker_warps * P.S);
+    if (P.arena_mode == kArenaNone) grow_run<D, Key, MODE, true>(P, smem, nullptr, P.worker_warps * P.S);
+    else grow_run<D, Key, MODE, false>(P, smem, nullptr, P.worker_warps * P.S);
 }
 
 // ---------------------------------------------------------------------------
@@ -1168,9 +1173,10 @@ __global__ void __launch_bounds__(32 * 9, 1) batch_kernel(const BatchDev B) {
         __syncthreads();
         const BatchLeave bl{B.runs_open, B.closed, B.active + r, helping != 0};
         const int cw = walks;
-        if (Ps.d == 2) grow_run<2, uint32_t, MODE>(Ps, smem, &bl, cw);
-        else if (Ps.n_max > 512) grow_run<3, unsigned long long, MODE>(Ps, smem, &bl, cw);
-        else grow_run<3, uint32_t, MODE>(Ps, smem, &bl, cw);
+        // a batch member's walks are laid out in shared memory (never the arena)
+        if (Ps.d == 2) grow_run<2, uint32_t, MODE, true>(Ps, smem, &bl, cw);
+        else if (Ps.n_max > 512) grow_run<3, unsigned long long, MODE, true>(Ps, smem, &bl, cw);
+        else grow_run<3, uint32_t, MODE, true>(Ps, smem, &bl, cw);
         __syncthreads();
         if (threadIdx.x == 0) atomicSub(B.active + r, 1);
         __syncthreads();

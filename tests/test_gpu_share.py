@@ -137,7 +137,9 @@ def test_helper_walks_need_shared_copies():
             assert run.stats()["slots"] == 4
     with Run(2, 32, 4, 1, helper_walks=0) as run:
         assert run.stats()["slots"] == 4
-    with Run(2, 32, 4, 1) as run:                    # default: the layout's spare walks
+    with Run(2, 32, 4, 1) as run:                    # default: none
+        assert run.stats()["slots"] == 4
+    with Run(2, 32, 4, 1, helper_walks=-1) as run:   # -1: the layout's spare walks
         assert run.stats()["slots"] > 4
 
 
