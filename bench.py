@@ -303,7 +303,9 @@ def autotuned_run(tours):
     w = WORKLOAD
     cfg = pb.make_config(w["d"], w["n_max"], w["n_seq"], w["seed"], max_seconds=120.0)
     t0 = time.perf_counter()
-    pb.autotune(cfg, probe_tours=32)
+    # probes of a quarter of the run: the tuner validates its pick on runs of
+    # four times the probe, i.e. on complete runs of this workload
+    pb.autotune(cfg, probe_tours=max(1, tours // 4))
     tune_s = time.perf_counter() - t0
     out = {"lanes_per_warp": cfg.lanes_per_warp, "hash_scale": cfg.hash_scale, "stack_ring": cfg.stack_ring,
            "tune_s": tune_s}

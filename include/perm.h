@@ -334,9 +334,10 @@ void perm_batch_destroy(perm_batch_handle b);
  * 2, 4, 8, 16, 32), hash size (hash_scale 0, 1) and stack ring (16, 64 records),
  * times a complete run of probe_tours tours per sequence of cfg from empty
  * tables (twice; the faster counts).  The default layout (auto, 0, 16) is timed
- * first and kept unless another choice is at least 3% faster and then faster
- * again on runs of 4 x probe_tours, so the pick is never slower than the
- * default on that validation.  Writes the choice into cfg->lanes_per_warp,
+ * first and kept unless another choice is at least 3% faster and then at least
+ * 3% faster again on runs of 4 x probe_tours (the fastest of three runs of each,
+ * alternated: complete runs vary by 10-30% in nodes), so the pick is never
+ * slower than the default on that validation.  Writes the choice into cfg->lanes_per_warp,
  * cfg->hash_scale and cfg->stack_ring.  Equal tours in every trial, so the
  * comparison is at equal work, start-up included.  Results are cached per (d,
  * n_max, n_seq, max_ctas, alg, threshold) for the process.  Synchronous;
