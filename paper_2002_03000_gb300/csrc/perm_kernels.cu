@@ -2,7 +2,7 @@
 // Campbell and Janse van Rensburg, "Parallel PERM", Sec. 3) for sm_103a.
 //
 // One thread grows one walk ("slot"); a warp holds up to 32 walks.  Per walk,
-// shared memory holds the occupancy hash (linear probing, deleted in LIFO
+// shared memory holds the occupancy hash (triangular probing, deleted in LIFO
 // order on backtrack), the hash slot of every site, and the top of the stack
 // of waiting copies (the rest spills to global memory).  Each thread runs the
 // tours handed to it one after another; a tour is a depth-first traversal of
