@@ -68,7 +68,7 @@ typedef struct {
     int threshold;     /* PERM_THRESH_SNAPSHOT or PERM_THRESH_FRESH (Alg. 2 only) */
     int slots;         /* concurrent walks on the GPU; 0 = min(N, device capacity) */
     int lanes_per_warp;/* walks per warp, 1..32; 0 = automatic (about four warps per SM) */
-    int refresh_ns;    /* snapshot refresh period in ns, paced on the global timer; 0 = default (8000) */
+    int refresh_ns;    /* snapshot refresh period in ns, paced on the SM cycle counter; 0 = default (8000) */
     double max_seconds;/* wall-clock bound of one launch; past it the kernel stops and the
                           run reports PERM_ETIMEOUT; 0 = default (600) */
     int ramp_c0;       /* Algorithm 2 admission: at most ramp_c0 + ramp_gamma * (finished
