@@ -337,10 +337,22 @@ def growth_constants(sq_estimates):
     from paper_2002_03000_gb300.analysis import fit_eq15
     out = {}
     lc2, rv2 = sq_estimates
+    import torch
     cub = pg.Run(3, 512, 8192, 1, max_seconds=120.0)
+    cub.run(128)                      # a warm-up run, then the timed one from empty tables
+    cub.reset()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
     cub.run(128)
+    el = time.perf_counter() - t0
     lc3, _, rv3 = cub.estimates()
+    steps3 = cub.stats()["steps"]
     cub.close()
+    out["cubic_run"] = {"workload": "d=3 n_max=512 8192 sequences x 128 tours, one complete run from empty tables",
+                        "seconds": el, "steps": steps3, "steps_per_s": steps3 / el,
+                        "rel_se_c_nmax": math.sqrt(rv3[-1]) if rv3[-1] >= 0 else None,
+                        "timing": "wall clock around the run, device synchronised on both sides (one run "
+                                  "after a warm-up run)"}
     for d, lc, rv in ((2, lc2, rv2), (3, lc3, rv3)):
         f = fit_eq15(lc, rv, n_min=64, n_max=len(lc) - 1)
         g = fit_eq15(lc, rv, n_min=64, n_max=len(lc) - 1, log_mu=LOG_MU_REF[d])
