@@ -316,6 +316,8 @@ int create_impl(perm_handle *out, const perm_config *cfg, const ForcedLayout *fo
     h->stride = stride;
     h->slots = (int)slots;
     h->smem = smem_for(warps, stride);
+    // the batch kernel grows its members with the shared-memory body only
+    if (force && arena_mode != perm::kArenaNone) { cudaStreamDestroy(h->stream); delete h; return PERM_EUNSUPPORTED; }
     h->arena_mode = arena_mode;
     if (arena_mode != perm::kArenaNone) {
         const size_t wb = perm::cta_warp_bytes(key64, n_max, log2h, h->stack_cache, stride);
