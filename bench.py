@@ -615,6 +615,46 @@ def long_walks(cap_s=60.0):
     return out
 
 
+def table2_long_walks(cap_s=300.0):
+    """Sec. 4, Table 2's setup: square lattice, n_max = 10^4, 12 sequences, no helper
+    walks (12 walks, as the paper's 12 threads), from empty tables; log c_10000 after
+    12 x 1, 12 x 10, 12 x 100 and 12 x 1000 walks (cumulative tours per sequence) for
+    Algorithm 2 (one shared table) and Algorithm 1 (private tables: the arithmetic
+    combination of Sec. 3 and the geometric one of Sec. 4), each algorithm stopped
+    once `cap_s` seconds have passed.  Opt-in (--table2): the Algorithm-1 leg takes
+    minutes."""
+    import paper_2002_03000_gb300 as pg
+    from paper_2002_03000_gb300.analysis import alg1_combine
+    paper = {"alg1": {1: 9273.79, 10: 9658.79, 100: 9692.63, 1000: 9703.54},
+             "alg2": {1: 9652.09, 10: 9697.79, 100: 9703.23, 1000: 9704.04}}
+    out = {"workload": "square lattice, n_max 10^4, 12 sequences, seed 1, no helper walks", "cap_s": cap_s}
+    for name, alg in (("alg2", pg.PERM_ALG2), ("alg1", pg.PERM_ALG1)):
+        rows = []
+        run = pg.Run(2, 10000, 12, 1, alg=alg, max_seconds=max(cap_s, 60.0))
+        done, t_all = 0, time.perf_counter()
+        for target in (1, 10, 100, 1000):
+            if time.perf_counter() - t_all > cap_s:
+                break
+            t0 = time.perf_counter()
+            try:
+                run.run(target - done)
+            except pg.PermError as e:
+                rows.append({"walks_per_seq": target, "error": str(e), "seconds": time.perf_counter() - t0})
+                break
+            done = target
+            lc = run.estimates()[0]
+            v = float(lc[10000])
+            row = {"walks_per_seq": target, "seconds": time.perf_counter() - t0,
+                   "log_c10000": v if math.isfinite(v) else None, "paper": paper[name][target]}
+            if alg == pg.PERM_ALG1:
+                gv = float(alg1_combine(run.tables(), 2, mode="geometric")[10000])
+                row["log_c10000_geometric"] = gv if math.isfinite(gv) else None
+            rows.append(row)
+        run.close()
+        out[name] = rows
+    return out
+
+
 def run_ours(args):
     import torch
     world, rank, local = dist_env()
@@ -762,6 +802,8 @@ def run_ours(args):
         line["alg1_vs_alg2"] = alg1_vs_alg2()
         line["perm_cutoffs"] = perm_cutoffs_vs_flatperm()
         line["long_walks"] = long_walks(args.long_cap_s)
+        if args.table2:
+            line["table2"] = table2_long_walks(args.table2_cap_s)
         line["autotune"] = autotuned_run(w["tours"])
         line["batched"] = batched_to_target(args.batch_target)
         line["batched"]["stand_in"] = ("stated config: each of the 96 runs to rel. SE of c_nmax <= 1e-3; "
@@ -793,6 +835,9 @@ def main():
     ap.add_argument("--skip-systems", action="store_true")
     ap.add_argument("--batch-target", type=float, default=3e-2)
     ap.add_argument("--long-cap-s", type=float, default=30.0)
+    ap.add_argument("--table2", action="store_true",
+                    help="also run Table 2's setup (n_max 10^4, 12 sequences) for both algorithms (minutes)")
+    ap.add_argument("--table2-cap-s", type=float, default=300.0)
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
